@@ -1,0 +1,407 @@
+"""Benchmark of the PTA-MD fine-burst engine on GB300.
+
+One bench step is one coarse step of the Practical Time Averaging protocol
+on the single large specimen: a 49^3-cell FCC Al cube (470,596 atoms) at
+300 K under tension at 1e-3 1/s with h = 1 s, i.e. three grip increments,
+three fine bursts of 5,000 velocity-Verlet steps (FP32 pair arithmetic,
+FP64 accumulators) and the coarse-step update.  The metric is atom-steps/s
+(atoms x fine steps per second), whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pta|reference]
+                    [--workload large|plain|batched|uneven]
+
+Under torchrun (N > 1) every rank advances its own specimen (independent
+replicas, no collective on the data path); the time is the maximum over
+ranks and the value counts the work of all ranks.  ``--impl reference``
+times the FP64 CPU oracle on this machine's host cores on bounded samples of
+the same workload (it is the reference arm: there is no other implementation
+of the method to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pta_inputs as PI  # noqa: E402
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "large": dict(name="large_fp32_n49", n_cells=49, T0=300.0, rate=1e-3, burst=5000,
+                  precision=1, count=1,
+                  desc="49^3-cell FCC Al cube (470,596 atoms), 300 K, tension 1e-3/s, h=1 s, "
+                       "3 bursts x 5,000 steps per coarse step, FP32 pair math, FP64 "
+                       "accumulators"),
+    "plain": dict(name="plain_fp64_n10", n_cells=10, T0=300.0, rate=1e-3, burst=2000,
+                  precision=0, count=1,
+                  desc="10^3-cell FCC Al cube (4,000 atoms), 300 K, tension 1e-3/s, "
+                       "3 bursts x 2,000 steps per coarse step, FP64 throughout"),
+    "batched": dict(name="batched_64x_n20", n_cells=20, T0=None, rate=None, burst=2000,
+                    precision=1, count=64,
+                    desc="64 replicas of a 20^3-cell cube (32,000 atoms each), T0 cycling "
+                         "10/100/300 K, half tension half compression, rates log-uniform "
+                         "1e-4..1e-3/s, 3 bursts x 2,000 steps per coarse step, one launch "
+                         "set per fine step for all replicas"),
+    "uneven": dict(name="uneven_28x_n10_49", n_cells=None, T0=300.0, rate=None, burst=2000,
+                   precision=1, count=28,
+                   desc="4 cubes each of 10,15,20,25,30,40,49 cells (3,786,384 atoms), "
+                        "alternating tension/compression, 300 K, 3 bursts x 2,000 steps"),
+}
+
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+N_SM = 152
+
+
+def perfect_lattice_pairs(n_cells: int, rc_over_a0: float = 2.0) -> int:
+    """Number of unordered atom pairs closer than rc in a perfect n^3-cell
+    FCC cube (counted exactly over lattice vectors, r < rc strict)."""
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    R = int(np.ceil(rc_over_a0)) + 1
+    total = 0
+    n = n_cells
+    for b1 in range(4):
+        for b2 in range(4):
+            d0 = basis[b2] - basis[b1]
+            for i in range(-R, R + 1):
+                for j in range(-R, R + 1):
+                    for k in range(-R, R + 1):
+                        d = d0 + np.array([i, j, k])
+                        r2 = float(d @ d)
+                        if r2 == 0.0 or not (r2 < rc_over_a0 ** 2):
+                            continue
+                        # cells c with c + (i,j,k) inside [0, n)^3
+                        total += (n - abs(i)) * (n - abs(j)) * (n - abs(k)) if \
+                            max(abs(i), abs(j), abs(k)) < n else 0
+    return total // 2
+
+
+# algorithmic floating-point operations (each add, multiply, divide, square
+# root counted once, a fused multiply-add twice), from the oracle's formulas:
+# per unordered pair within rc: density pass 19, force pass 41; per atom and
+# step 33 (embedding, two half-kicks, drift, kinetic and potential energy)
+FLOP_DENSITY_PAIR = 19
+FLOP_FORCE_PAIR = 41
+FLOP_ATOM = 33
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int = 0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            uuid = os.environ.get("PTA_GPU_UUID")
+            if uuid:
+                cmd += ["-i", uuid]
+            else:
+                cmd += ["-i", str(self.dev)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _requests(wl, rank):
+    if wl["name"].startswith("batched"):
+        return PI.config_batched(64, 20)
+    if wl["name"].startswith("uneven"):
+        return PI.config_uneven()
+    return [PI.SpecimenRequest(n_cells=wl["n_cells"], T0=wl["T0"], seed=1 + rank,
+                               strain_rate=wl["rate"], burst_steps=wl["burst"])]
+
+
+# ---------------------------------------------------------------------------
+# own arm
+# ---------------------------------------------------------------------------
+def run_pta(args, wl):
+    import torch
+    import paper_2603_07321_gb300 as P
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    P.build()
+    reqs = _requests(wl, rank)
+    ctxs = []
+    for r in reqs:
+        ctxs.append(P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=wl["precision"],
+                          burst_steps=r.burst_steps, strain_rate=r.strain_rate))
+    natoms = sum(c.n for c in ctxs)
+    batch = P.Batch(ctxs) if len(ctxs) > 1 else None
+    stepper = batch if batch is not None else ctxs[0]
+
+    def one_step():
+        if batch is not None:
+            return batch.coarse_step()
+        return [ctxs[0].coarse_step()]
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stepper.set_timing(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(st)
+    results = []
+    for _ in range(args.steps):
+        results.append(one_step())
+    e1.record(st)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kt = stepper.timing()
+    stepper.set_timing(False)
+    t_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    fine_per_step = 3 * max(r.burst_steps for r in reqs)
+    atom_steps_rank = sum(c.n * 3 * r.burst_steps for c, r in zip(ctxs, reqs)) * args.steps
+    value = atom_steps_rank * ws / (t_max / 1e3)
+
+    # live roofline of the dominant kernel (the force pass): algorithmic flops
+    # per launch / mean CUDA-event duration of the launch in the timed region
+    pairs = sum(perfect_lattice_pairs(r.n_cells) for r in reqs)
+    iters = max(kt.iterations, 1)
+    force_ms = kt.force_ms / iters
+    dens_ms = kt.density_ms / iters
+    flops_force = pairs * FLOP_FORCE_PAIR + natoms * (FLOP_ATOM - 5)
+    flops_dens = pairs * FLOP_DENSITY_PAIR + natoms * 5
+    clk = clocks["sm_max_mhz"] or 2070.0
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    ach_force = flops_force / (force_ms / 1e3) / 1e12
+    ach_dens = flops_dens / (dens_ms / 1e3) / 1e12
+    dominant = ("force", ach_force, force_ms) if force_ms >= dens_ms else ("density", ach_dens,
+                                                                           dens_ms)
+
+    # launches of this library's kernels in the timed region
+    bursts = 3 * args.steps
+    groups = len({(c.params.precision, 0) for c in ctxs})
+    launches = int(kt.iterations * (7 + 2 * groups) + bursts * 3 + args.steps)
+
+    # end to end through the public API with host buffers: per step the state
+    # goes host -> device from pinned memory, the coarse step runs, and the
+    # state and result come back to pinned host memory
+    e2e = None
+    if batch is None:
+        c = ctxs[0]
+        hpos = torch.empty((c.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        hvel = torch.empty((c.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        p, v = c.get_state()
+        hpos[:] = p
+        hvel[:] = v
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            c.set_state(hpos, hvel)
+            c.coarse_step()
+            p, v = c.get_state()
+            hpos[:] = p
+            hvel[:] = v
+        barrier()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        nb = c.n * 6 * 8
+        e2e = {"value": atom_steps_rank * ws / dt, "unit": "atom-steps/s",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 3 * 416}
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(wl, reqs[0].n_cells) if (ws == 1 and not args.no_cpu) else None
+        out = {
+            "metric": "atom-steps/s",
+            "value": value,
+            "unit": "atom-steps/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if wl["precision"] == 1 else "f64",
+            "data": "synthetic (FCC lattice + seeded Maxwell-Boltzmann velocities)",
+            "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
+                       "specimens": len(ctxs), "fine_steps_per_step": fine_per_step,
+                       "accumulators": "f64", "l2": "working set > 129 MB L2 (no flush)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_%s_f32" % dominant[0]
+                         if wl["precision"] == 1 else "k_%s_f64" % dominant[0],
+                         "achieved": dominant[1], "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": dominant[1] / peak_tflops, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz "
+                                        "(recipe unit counts, measured max clock)" % clk,
+                         "launch_ms": dominant[2],
+                         "kernels_ms_per_iteration": {"rebuild": kt.rebuild_ms / iters,
+                                                      "density": dens_ms, "force": force_ms}},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if batch is not None:
+        batch.close()
+    for c in ctxs:
+        c.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(wl, n_cells, target_s: float = 15.0):
+    """The FP64 oracle timed on this machine's host cores on a bounded
+    sample of the same workload (a few velocity-Verlet steps of one cube)."""
+    import oracle as O
+    O.build()
+    spec = O.Specimen(n_cells)
+    spec.thermalise(300.0, 1)
+    spec.apply_strain(1e-3)
+    t = time.perf_counter()
+    spec.burst(1)
+    one = time.perf_counter() - t
+    steps = int(max(2, min(200, target_s / max(one, 1e-6))))
+    t = time.perf_counter()
+    spec.burst(steps)
+    dt = time.perf_counter() - t
+    return {"value": spec.n * steps / dt, "unit": "atom-steps/s",
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+            "kind": "oracle",
+            "sample": "%d velocity-Verlet steps of the %d-atom cube (FP64 oracle, OpenMP over "
+                      "atoms, pairs found anew every step)" % (steps, spec.n)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, wl):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import oracle as O
+    O.build()
+    n_cells = wl["n_cells"] or 49
+    spec = O.Specimen(n_cells)
+    spec.thermalise(300.0, 1)
+    spec.apply_strain(1e-3)
+    sample_steps = args.ref_sample
+    for _ in range(args.warmup):
+        spec.burst(sample_steps)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        spec.burst(sample_steps)
+    dt = time.perf_counter() - t
+    value = spec.n * sample_steps * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = ("each step: %d velocity-Verlet steps of the %d-atom cube (FP64 oracle, OpenMP "
+              "over atoms)" % (sample_steps, spec.n))
+    out = {"impl": "reference", "metric": "atom-steps/s", "value": value,
+           "unit": "atom-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["name"], "description": wl["desc"]},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value,
+                            "unit": "atom-steps/s"},
+           "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pta", choices=["pta", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--ref-sample", type=int, default=4,
+                    help="fine steps per reference-arm step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_pta(args, wl)
+
+
+if __name__ == "__main__":
+    main()

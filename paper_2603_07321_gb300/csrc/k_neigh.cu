@@ -1,0 +1,253 @@
+// Cell binning by counting sort and Verlet-list construction.
+//
+// The list of atom i holds every j != i with |r_j - r_i|^2 < (rc + skin)^2,
+// the squared distance formed as (dx*dx + dy*dy) + dz*dz in FP64 without
+// contraction.  Candidates come from the 27 cells around i's cell on a grid
+// of edge >= rc + skin; atoms outside the grid are clamped onto its border
+// cells, which keeps every pair within reach (clamping is non-expansive).
+// Cells are visited in increasing linear index and each cell's atoms in
+// increasing atom index, so a list's order depends only on the grid and the
+// positions: builds are deterministic.
+//
+// The list is rebuilt only when the force kernel found an atom that moved
+// more than skin/2 since the last build (or on request); every kernel here
+// returns at once for a specimen that needs no build.
+#include "pta_dev.cuh"
+
+namespace pta {
+
+__device__ __forceinline__ bool build_active(const SpecDev &S, int force) {
+    const SpecCtl *c = S.ctl;
+    if (force) return true;
+    if (c->phase == PH_IDLE) return false;
+    return c->rebuild != 0 || c->list_L != S.L;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// position of atom a in FP64 (exact value of the stored representation)
+__device__ __forceinline__ void load_pos64(const SpecDev &S, int par, int a, double &x, double &y,
+                                           double &z) {
+    if (S.prec == PTA_PREC_FP64) {
+        const double4_32a q = ((const double4_32a *)S.pos[par])[a];
+        x = q.x;
+        y = q.y;
+        z = q.z;
+    } else {
+        const float4 h = ((const float4 *)S.pos[par])[a];
+        const float4 l = S.lo[par][a];
+        x = (double)h.x + (double)l.x;
+        y = (double)h.y + (double)l.y;
+        z = (double)h.z + (double)l.z;
+    }
+}
+
+__global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__ b2s, int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (a >= S.n) return;
+    const int par = S.ctl->parity;
+    double x[3];
+    load_pos64(S, par, a, x[0], x[1], x[2]);
+    int ci[3];
+    for (int d = 0; d < 3; ++d)
+        ci[d] = clampi((int)floor((x[d] - S.org[d]) * S.inv_h), 0, S.nc[d] - 1);
+    const int c = ci[0] + S.nc[0] * (ci[1] + S.nc[1] * ci[2]);
+    S.atom_cell[a] = c;
+    atomicAdd(&S.cell_cnt[c], 1);
+}
+
+// one block per specimen: exclusive scan of the cell counts; counts reset to
+// 0 for use as fill counters by the scatter
+__global__ void k_scan(const SpecDev *__restrict__ specs, int force) {
+    const SpecDev &S = specs[blockIdx.x];
+    if (!build_active(S, force)) return;
+    __shared__ int wsum[SCAN_THREADS / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
+        const int c = base + threadIdx.x;
+        const int v = (c < S.ncell) ? S.cell_cnt[c] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
+        if (c < S.ncell) {
+            S.cell_start[c] = excl;
+            S.cell_cnt[c] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        S.cell_start[S.ncell] = carry;
+        S.ctl->rebuilds += 1;
+    }
+}
+
+__global__ void k_scatter(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                          int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (a >= S.n) return;
+    const int c = S.atom_cell[a];
+    const int slot = S.cell_start[c] + atomicAdd(&S.cell_cnt[c], 1);
+    S.cell_tmp[slot] = a;
+}
+
+// one warp per cell: order the cell's atoms by index (rank = number of
+// smaller indices), then clear the cell's counter for the next build
+__global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                            int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int c = (blockIdx.x - S.blk_cell0) * CELL_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= S.ncell) return;
+    const int s = S.cell_start[c], e = S.cell_start[c + 1];
+    for (int p = s + lane; p < e; p += 32) {
+        const int v = S.cell_tmp[p];
+        int r = 0;
+        for (int q = s; q < e; ++q) r += (S.cell_tmp[q] < v);
+        S.cell_atoms[s + r] = v;
+    }
+    if (lane == 0) S.cell_cnt[c] = 0;
+}
+
+// one thread per atom: scan the 27 cells around the atom's cell
+__global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs,
+                                               const int *__restrict__ b2s, int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    const int par = S.ctl->parity;
+    int cnt = 0;
+    if (a < S.n) {
+        double xa, ya, za;
+        load_pos64(S, par, a, xa, ya, za);
+        const int c = S.atom_cell[a];
+        const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
+        const long long base = nl_base(a, S.L, S.cap);
+        const int L = S.L;
+        const bool mixed = S.prec != PTA_PREC_FP64;
+        float4 ha = make_float4(0, 0, 0, 0), la = ha;
+        if (mixed) {
+            ha = ((const float4 *)S.pos[par])[a];
+            la = S.lo[par][a];
+        }
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= S.nc[2]) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= S.nc[1]) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = cx + dx;
+                    if (x < 0 || x >= S.nc[0]) continue;
+                    const int cc = x + S.nc[0] * (y + S.nc[1] * z);
+                    const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
+                    for (int p = s; p < e; ++p) {
+                        const int j = S.cell_atoms[p];
+                        if (j == a) continue;
+                        bool in;
+                        if (mixed) {
+                            // FP32 distance first; only the thin band around the list
+                            // radius is decided by the exact FP64 test
+                            const float4 hj = ((const float4 *)S.pos[par])[j];
+                            const float4 lj = S.lo[par][j];
+                            const float fx = (hj.x - ha.x) + (lj.x - la.x);
+                            const float fy = (hj.y - ha.y) + (lj.y - la.y);
+                            const float fz = (hj.z - ha.z) + (lj.z - la.z);
+                            const float r2f = fx * fx + fy * fy + fz * fz;
+                            if (r2f < S.f_rl2_lo) {
+                                in = true;
+                            } else if (r2f >= S.f_rl2_hi) {
+                                in = false;
+                            } else {
+                                const double ddx = ((double)hj.x + (double)lj.x) - xa;
+                                const double ddy = ((double)hj.y + (double)lj.y) - ya;
+                                const double ddz = ((double)hj.z + (double)lj.z) - za;
+                                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx),
+                                                                      __dmul_rn(ddy, ddy)),
+                                                            __dmul_rn(ddz, ddz));
+                                in = r2 < S.rl2;
+                            }
+                        } else {
+                            const double4_32a q = ((const double4_32a *)S.pos[par])[j];
+                            const double ddx = q.x - xa, ddy = q.y - ya, ddz = q.z - za;
+                            const double r2 = __dadd_rn(
+                                __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                __dmul_rn(ddz, ddz));
+                            in = r2 < S.rl2;
+                        }
+                        if (in) {
+                            if (cnt < S.cap) S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] = j;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+        }
+        S.nn[a] = cnt < S.cap ? cnt : S.cap;
+        S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
+    }
+    // block maximum of the counts, one atomic per block
+    __shared__ int smax[TPB / 32];
+    int m = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TPB / 32; ++w) m = max(m, smax[w]);
+        m = max(m, smax[0]);
+        atomicMax(&S.ctl->max_nn, m);
+        if (m > S.cap) atomicOr(&S.ctl->err, ERR_OVERFLOW);
+    }
+}
+
+// after the build: record the layout the list was built for (a separate
+// kernel, so that the gate above reads the same value in every block)
+__global__ void k_build_done(const SpecDev *__restrict__ specs, int force) {
+    const SpecDev &S = specs[blockIdx.x];
+    if (!build_active(S, force)) return;
+    if (threadIdx.x == 0) S.ctl->list_L = S.L;
+}
+
+__global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
+    const SpecDev &S = specs[blockIdx.x];
+    if (!build_active(S, force)) return;
+    if (threadIdx.x == 0) S.ctl->max_nn = 0;
+}
+
+void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
+    k_reset_maxnn<<<t.nspec, 32, 0, st>>>(t.specs, force);
+    k_bin<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_scan<<<t.nspec, SCAN_THREADS, 0, st>>>(t.specs, force);
+    k_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_cell_sort<<<t.nblk_cell, CELL_WARPS * 32, 0, st>>>(t.specs, t.b2s_cell, force);
+    k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);
+}
+
+}  // namespace pta

@@ -1,0 +1,131 @@
+// Pieces shared by the FP64 and mixed-precision pair kernels: warp
+// reductions and the end-of-step reduction that turns per-block partials
+// into the state functions K, U, T of Eq. (state_variables) for one step.
+#pragma once
+
+#include "pta_dev.cuh"
+
+namespace pta {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// sum over the L lanes that share one atom (lanes are contiguous in the warp)
+template <int L, typename T>
+__device__ __forceinline__ T lane_sum(T v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Called by every thread of a pair block after the warp reductions (values
+// valid in lane 0 of each warp).  Block partials go to S.part; the last
+// block of the specimen to finish sums all partials in a fixed order and
+// advances the specimen's control block:
+//   MODE_STEP, phase RUN:     sample (K, U, T) into the series, step count + 1,
+//                             burst over after nsteps samples
+//   MODE_STEP, phase REFRESH: forces refreshed and the first step started
+//   MODE_EVAL:                K, U, T stored in eval_obs
+// and in MODE_STEP the position buffers swap and the skin test sets the
+// rebuild flag.
+__device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double pe_w, double rr_w,
+                                 double d2_w, int mode, int phase, long long done,
+                                 long long nsteps) {
+    __shared__ double shw[4][TPB / 32];
+    __shared__ double red[4][TPB];
+    __shared__ int is_last;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        shw[0][w] = ke_w;
+        shw[1][w] = pe_w;
+        shw[2][w] = rr_w;
+        shw[3][w] = d2_w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double k = 0, p = 0, r = 0, d = 0;
+        for (int i = 0; i < TPB / 32; ++i) {
+            k = k + shw[0][i];
+            p = p + shw[1][i];
+            r = r + shw[2][i];
+            d = fmax(d, shw[3][i]);
+        }
+        double *P = S.part + 4LL * lb;
+        P[0] = k;
+        P[1] = p;
+        P[2] = r;
+        P[3] = d;
+        __threadfence();
+        const unsigned prev = atomicAdd(&S.ctl->blocks_done, 1u);
+        is_last = (prev == (unsigned)(S.nblk_pair - 1));
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double k = 0, p = 0, r = 0, d = 0;
+    for (int b = threadIdx.x; b < S.nblk_pair; b += TPB) {
+        const double *P = S.part + 4LL * b;
+        k = k + __ldcg(P);
+        p = p + __ldcg(P + 1);
+        r = r + __ldcg(P + 2);
+        d = fmax(d, __ldcg(P + 3));
+    }
+    red[0][threadIdx.x] = k;
+    red[1][threadIdx.x] = p;
+    red[2][threadIdx.x] = r;
+    red[3][threadIdx.x] = d;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] = red[0][threadIdx.x] + red[0][threadIdx.x + s];
+            red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + s];
+            red[2][threadIdx.x] = red[2][threadIdx.x] + red[2][threadIdx.x + s];
+            red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    SpecCtl *c = S.ctl;
+    const double K = red[0][0], U = red[1][0], T = red[2][0] * S.t_fac, md2 = red[3][0];
+    if (mode == MODE_EVAL) {
+        c->eval_obs[0] = K;
+        c->eval_obs[1] = U;
+        c->eval_obs[2] = T;
+        c->rebuild = 0;
+    } else {
+        if (phase == PH_RUN) {
+            if (!isfinite(K) || !isfinite(U) || !isfinite(T)) {
+                c->err |= ERR_NAN;
+                c->phase = PH_IDLE;
+            } else {
+                double *o = S.series + 3 * done;
+                o[0] = K;
+                o[1] = U;
+                o[2] = T;
+                c->sum[0] = c->sum[0] + K;
+                c->sum[1] = c->sum[1] + U;
+                c->sum[2] = c->sum[2] + T;
+                c->done = done + 1;
+                if (done + 1 >= nsteps) c->phase = PH_IDLE;
+            }
+        } else if (phase == PH_REFRESH) {
+            c->phase = PH_RUN;
+        }
+        c->rebuild = (md2 > (double)S.half_skin2) ? 1 : 0;
+        c->parity ^= 1;
+    }
+    __threadfence();
+    c->blocks_done = 0;
+}
+
+}  // namespace pta

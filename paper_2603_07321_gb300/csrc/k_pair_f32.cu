@@ -1,0 +1,261 @@
+// Mixed-precision pair kernels: Sutton-Chen EAM density and forces in FP32
+// on relative coordinates, positions kept as an exact FP32 pair x = hi + lo
+// (hi on a 2^-12 A grid, |lo| <= 2^-13 A), so that
+//     r_j - r_i = (hi_j - hi_i) + (lo_j - lo_i)
+// is formed with the first difference exact; velocities FP32; energies,
+// stresses and time averages reduced in FP64.
+//
+// Pass 1 (density): rho_i = sum_j phi_m(r_ij), then B'(rho_i) =
+// -eps c / (2 sqrt(rho_i)) stored beside lo_i.  Eq. (pe).
+// Pass 2 (force):   F_i = sum_j [eps phi_n'(r) + (B'_i + B'_j) phi_m'(r)] (r_j - r_i)/r,
+// Eq. (f_int), the per-atom energy 1/2 eps sum_j phi_n + B(rho_i), and the
+// velocity-Verlet update of Eqs. (vv_algo_*) fused behind it: the second
+// half-kick that finishes the step, the sample of K, U, T, and (unless the
+// burst ends) the first half-kick and drift of the next step.  Grip atoms
+// keep v = 0 and F = 0 in the update; their internal force still enters the
+// reaction R = -sum_{right grip} F . e of Eq. (state_variables).
+#include "k_pair_common.cuh"
+
+namespace pta {
+
+template <bool SC76>
+struct PowF {
+    // s^m and s^n for the Sutton-Chen exponents
+    __device__ __forceinline__ static void pw(float s, int n, int m, float &sn, float &sm) {
+        if (SC76) {
+            const float s2 = s * s, s3 = s2 * s;
+            sm = s3 * s3;
+            sn = sm * s;
+        } else {
+            float p = 1.f, q = 1.f;
+            for (int i = 0; i < m; ++i) p *= s;
+            for (int i = 0; i < n; ++i) q *= s;
+            sm = p;
+            sn = q;
+        }
+    }
+    __device__ __forceinline__ static float pm(float s, int m) {
+        if (SC76) {
+            const float s2 = s * s, s3 = s2 * s;
+            return s3 * s3;
+        }
+        float p = 1.f;
+        for (int i = 0; i < m; ++i) p *= s;
+        return p;
+    }
+};
+
+template <int L, bool SC76>
+__global__ void __launch_bounds__(TPB) k_density_f32(const SpecDev *__restrict__ specs,
+                                                     const int *__restrict__ b2s, int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    const SpecCtl *ctl = S.ctl;
+    if (!force && ctl->phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    constexpr int APB = TPB / L;
+    const int a = (blockIdx.x - S.blk_pair0) * APB + threadIdx.x / L;
+    const int l = threadIdx.x % L;
+    const bool valid = a < S.n;
+    const float4 *__restrict__ hi = (const float4 *)S.pos[par];
+    const float4 *__restrict__ lo = S.lo[par];
+    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, Am = S.pot.f_Am, Bm = S.pot.f_Bm,
+                rc = S.pot.f_rc;
+    const int m = S.pot.m;
+    float rho = 0.f;
+    float4 hia = make_float4(0, 0, 0, 0), loa = hia;
+    if (valid) {
+        hia = hi[a];
+        loa = lo[a];
+        const int nn = S.nn[a];
+        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+        for (int k = l; k < nn; k += L) {
+            const int j = __ldg(lst + (k / L) * 32 + (k % L));
+            const float4 hj = __ldg(hi + j);
+            const float4 lj = __ldg(lo + j);
+            const float dx = (hj.x - hia.x) + (lj.x - loa.x);
+            const float dy = (hj.y - hia.y) + (lj.y - loa.y);
+            const float dz = (hj.z - hia.z) + (lj.z - loa.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2) {
+                const float ir = rsqrtf(r2);
+                const float r = r2 * ir;
+                const float s = pa * ir;
+                rho += PowF<SC76>::pm(s, m) - Am + Bm * (r - rc);
+            }
+        }
+    }
+    rho = lane_sum<L>(rho);
+    if (valid && l == 0) {
+        const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
+        ((float4 *)S.posfp)[a] = make_float4(loa.x, loa.y, loa.z, fp);
+    }
+}
+
+template <int L, bool SC76>
+__global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ specs,
+                                                   const int *__restrict__ b2s, int mode) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    SpecCtl *ctl = S.ctl;
+    const int phase = ctl->phase;
+    if (mode == MODE_STEP && phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    const long long done = ctl->done, nsteps = ctl->nsteps;
+    constexpr int APB = TPB / L;
+    const int lb = blockIdx.x - S.blk_pair0;
+    const int a = lb * APB + threadIdx.x / L;
+    const int l = threadIdx.x % L;
+    const bool valid = a < S.n;
+    const float4 *__restrict__ hi = (const float4 *)S.pos[par];
+    const float4 *__restrict__ lf = (const float4 *)S.posfp;
+    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, rc = S.pot.f_rc;
+    const float An = S.pot.f_An, Bn = S.pot.f_Bn, Bm = S.pot.f_Bm, eps = S.pot.f_eps;
+    const int n = S.pot.n, m = S.pot.m;
+    const float fn = (float)n, fm = (float)m;
+    float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f;
+    float4 hia = make_float4(0, 0, 0, 0), lfa = hia;
+    if (valid) {
+        hia = hi[a];
+        lfa = lf[a];
+        const int nn = S.nn[a];
+        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+        for (int k = l; k < nn; k += L) {
+            const int j = __ldg(lst + (k / L) * 32 + (k % L));
+            const float4 hj = __ldg(hi + j);
+            const float4 lj = __ldg(lf + j);
+            const float dx = (hj.x - hia.x) + (lj.x - lfa.x);
+            const float dy = (hj.y - hia.y) + (lj.y - lfa.y);
+            const float dz = (hj.z - hia.z) + (lj.z - lfa.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2) {
+                const float ir = rsqrtf(r2);
+                const float r = r2 * ir;
+                const float s = pa * ir;
+                float sn, sm;
+                PowF<SC76>::pw(s, n, m, sn, sm);
+                const float dphn = -fn * sn * ir + Bn;
+                const float dphm = -fm * sm * ir + Bm;
+                const float g = (eps * dphn + (lfa.w + lj.w) * dphm) * ir;
+                fx += g * dx;
+                fy += g * dy;
+                fz += g * dz;
+                en += sn - An + Bn * (r - rc);
+            }
+        }
+    }
+    fx = lane_sum<L>(fx);
+    fy = lane_sum<L>(fy);
+    fz = lane_sum<L>(fz);
+    en = lane_sum<L>(en);
+    float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f;
+    if (valid && l == 0) {
+        const float fpa = lfa.w;
+        pe = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
+        const uint8_t flag = S.flags[a];
+        if (flag == FLAG_RIGHT) rr = -(S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
+        float4 v = ((const float4 *)S.vel)[a];
+        if (mode == MODE_EVAL) {
+            ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+            double4_32a *o = (double4_32a *)S.eval_out;
+            o[a] = make_double4_32a(fx, fy, fz, pe);
+        } else {
+            const float kh = S.f_acc_half;
+            if (phase == PH_RUN) {
+                if (flag == FLAG_MOBILE) {
+                    v.x += fx * kh;
+                    v.y += fy * kh;
+                    v.z += fz * kh;
+                }
+                ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+            float h[3] = {hia.x, hia.y, hia.z}, q[3] = {lfa.x, lfa.y, lfa.z};
+            const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
+            if (start && flag == FLAG_MOBILE) {
+                v.x += fx * kh;
+                v.y += fy * kh;
+                v.z += fz * kh;
+                const float dt = S.f_dt;
+                q[0] += v.x * dt;
+                q[1] += v.y * dt;
+                q[2] += v.z * dt;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    // move whole grid quanta from lo to hi (both steps exact)
+                    const float sh = rintf(q[d] * (float)HI_SCALE) * (float)HI_QUANTUM;
+                    h[d] = h[d] + sh;
+                    q[d] = q[d] - sh;
+                }
+                if (fabsf(h[0]) > (float)MIXED_RANGE || fabsf(h[1]) > (float)MIXED_RANGE ||
+                    fabsf(h[2]) > (float)MIXED_RANGE)
+                    atomicOr(&ctl->err, ERR_RANGE);
+            }
+            ((float4 *)S.pos[par ^ 1])[a] = make_float4(h[0], h[1], h[2], 0.f);
+            S.lo[par ^ 1][a] = make_float4(q[0], q[1], q[2], 0.f);
+            ((float4 *)S.vel)[a] = v;
+            const float4 rf = S.ref[a];
+            const float ex = (h[0] - rf.x) + q[0], ey = (h[1] - rf.y) + q[1],
+                        ez = (h[2] - rf.z) + q[2];
+            d2 = ex * ex + ey * ey + ez * ez;
+        }
+    }
+    ke = warp_sum(ke);
+    pe = warp_sum(pe);
+    rr = warp_sum(rr);
+    d2 = warp_max(d2);
+    step_tail(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, mode, phase, done, nsteps);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch by (lanes, potential variant)
+// ---------------------------------------------------------------------------
+void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st);
+void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st);
+
+template <bool SC76>
+static void density_f32(const Tab &t, const Group &g, int force, cudaStream_t st) {
+    switch (g.L) {
+        case 1: k_density_f32<1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 2: k_density_f32<2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 4: k_density_f32<4, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 8: k_density_f32<8, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        default: k_density_f32<16, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+    }
+}
+
+template <bool SC76>
+static void force_f32(const Tab &t, const Group &g, int mode, cudaStream_t st) {
+    switch (g.L) {
+        case 1: k_force_f32<1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 2: k_force_f32<2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 4: k_force_f32<4, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 8: k_force_f32<8, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        default: k_force_f32<16, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+    }
+}
+
+void launch_density(const Tab &t, int force, cudaStream_t st) {
+    for (int i = 0; i < t.ngroups; ++i) {
+        const Group &g = t.grp[i];
+        if (g.nblk <= 0) continue;
+        if (g.prec == PTA_PREC_FP64)
+            launch_density_f64(t, g, force, st);
+        else if (g.sc76)
+            density_f32<true>(t, g, force, st);
+        else
+            density_f32<false>(t, g, force, st);
+    }
+}
+
+void launch_force(const Tab &t, int mode, cudaStream_t st) {
+    for (int i = 0; i < t.ngroups; ++i) {
+        const Group &g = t.grp[i];
+        if (g.nblk <= 0) continue;
+        if (g.prec == PTA_PREC_FP64)
+            launch_force_f64(t, g, mode, st);
+        else if (g.sc76)
+            force_f32<true>(t, g, mode, st);
+        else
+            force_f32<false>(t, g, mode, st);
+    }
+}
+
+}  // namespace pta

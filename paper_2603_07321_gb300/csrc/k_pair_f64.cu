@@ -1,0 +1,158 @@
+// FP64 pair kernels: the same two passes as the mixed-precision kernels
+// (density, then forces with the fused velocity-Verlet epilogue), with every
+// quantity in double.  They serve the plain FP64 form of the method and the
+// parity checks against the FP64 oracle.
+#include "k_pair_common.cuh"
+
+namespace pta {
+
+__device__ __forceinline__ double ipow(double s, int k) {
+    double p = 1.0;
+    for (int i = 0; i < k; ++i) p *= s;
+    return p;
+}
+
+template <int L>
+__global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__ specs,
+                                                     const int *__restrict__ b2s, int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    const SpecCtl *ctl = S.ctl;
+    if (!force && ctl->phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    constexpr int APB = TPB / L;
+    const int a = (blockIdx.x - S.blk_pair0) * APB + threadIdx.x / L;
+    const int l = threadIdx.x % L;
+    const bool valid = a < S.n;
+    const double4_32a *__restrict__ pos = (const double4_32a *)S.pos[par];
+    const PotDev &P = S.pot;
+    double rho = 0.0;
+    double4_32a pa = make_double4_32a(0, 0, 0, 0);
+    if (valid) {
+        pa = pos[a];
+        const int nn = S.nn[a];
+        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+        for (int k = l; k < nn; k += L) {
+            const int j = lst[(k / L) * 32 + (k % L)];
+            const double4_32a pj = pos[j];
+            const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
+            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
+            if (r < P.rc) rho += ipow(P.a / r, P.m) - P.Am + P.Bm * (r - P.rc);
+        }
+    }
+    rho = lane_sum<L>(rho);
+    if (valid && l == 0) {
+        const double fp = rho > 0.0 ? -P.ec / (2.0 * sqrt(rho)) : 0.0;
+        ((double4_32a *)S.posfp)[a] = make_double4_32a(pa.x, pa.y, pa.z, fp);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ specs,
+                                                   const int *__restrict__ b2s, int mode) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    SpecCtl *ctl = S.ctl;
+    const int phase = ctl->phase;
+    if (mode == MODE_STEP && phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    const long long done = ctl->done, nsteps = ctl->nsteps;
+    constexpr int APB = TPB / L;
+    const int lb = blockIdx.x - S.blk_pair0;
+    const int a = lb * APB + threadIdx.x / L;
+    const int l = threadIdx.x % L;
+    const bool valid = a < S.n;
+    const double4_32a *__restrict__ pf = (const double4_32a *)S.posfp;
+    const PotDev &P = S.pot;
+    double fx = 0, fy = 0, fz = 0, en = 0;
+    double4_32a pa = make_double4_32a(0, 0, 0, 0);
+    if (valid) {
+        pa = pf[a];
+        const int nn = S.nn[a];
+        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+        for (int k = l; k < nn; k += L) {
+            const int j = lst[(k / L) * 32 + (k % L)];
+            const double4_32a pj = pf[j];
+            const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
+            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
+            if (r < P.rc) {
+                const double s = P.a / r;
+                const double sn = ipow(s, P.n), sm = ipow(s, P.m);
+                const double dphn = -(double)P.n / r * sn + P.Bn;
+                const double dphm = -(double)P.m / r * sm + P.Bm;
+                const double g = (P.eps * dphn + (pa.w + pj.w) * dphm) / r;
+                fx += g * dx;
+                fy += g * dy;
+                fz += g * dz;
+                en += sn - P.An + P.Bn * (r - P.rc);
+            }
+        }
+    }
+    fx = lane_sum<L>(fx);
+    fy = lane_sum<L>(fy);
+    fz = lane_sum<L>(fz);
+    en = lane_sum<L>(en);
+    double ke = 0, pe = 0, rr = 0, d2 = 0;
+    if (valid && l == 0) {
+        const double fpa = pa.w;
+        // B(rho) = -eps c sqrt(rho) = (eps c)^2 / (2 B'(rho))
+        pe = 0.5 * P.eps * en + (fpa != 0.0 ? 0.5 * P.ec * P.ec / fpa : 0.0);
+        const uint8_t flag = S.flags[a];
+        if (flag == FLAG_RIGHT) rr = -(S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
+        double4_32a v = ((const double4_32a *)S.vel)[a];
+        if (mode == MODE_EVAL) {
+            ke = S.ke_fac * ((v.x * v.x + v.y * v.y) + v.z * v.z);
+            ((double4_32a *)S.eval_out)[a] = make_double4_32a(fx, fy, fz, pe);
+        } else {
+            const double kh = S.acc_half;
+            if (phase == PH_RUN) {
+                if (flag == FLAG_MOBILE) {
+                    v.x += fx * kh;
+                    v.y += fy * kh;
+                    v.z += fz * kh;
+                }
+                ke = S.ke_fac * ((v.x * v.x + v.y * v.y) + v.z * v.z);
+            }
+            double x = pa.x, y = pa.y, z = pa.z;
+            const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
+            if (start && flag == FLAG_MOBILE) {
+                v.x += fx * kh;
+                v.y += fy * kh;
+                v.z += fz * kh;
+                x += v.x * S.dt;
+                y += v.y * S.dt;
+                z += v.z * S.dt;
+            }
+            ((double4_32a *)S.pos[par ^ 1])[a] = make_double4_32a(x, y, z, 0.0);
+            ((double4_32a *)S.vel)[a] = v;
+            const float4 rf = S.ref[a];
+            const double ex = x - rf.x, ey = y - rf.y, ez = z - rf.z;
+            d2 = ex * ex + ey * ey + ez * ez;
+        }
+    }
+    ke = warp_sum(ke);
+    pe = warp_sum(pe);
+    rr = warp_sum(rr);
+    d2 = (double)warp_max((float)d2);
+    step_tail(S, lb, ke, pe, rr, d2, mode, phase, done, nsteps);
+}
+
+void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st) {
+    switch (g.L) {
+        case 1: k_density_f64<1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 2: k_density_f64<2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 4: k_density_f64<4><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        case 8: k_density_f64<8><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+        default: k_density_f64<16><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+    }
+}
+
+void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st) {
+    switch (g.L) {
+        case 1: k_force_f64<1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 2: k_force_f64<2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 4: k_force_f64<4><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        case 8: k_force_f64<8><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+        default: k_force_f64<16><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
+    }
+}
+
+}  // namespace pta

@@ -1,0 +1,158 @@
+// Device-side data structures of the fine-burst engine.
+//
+// One specimen on the device is described by a SpecDev (sizes, constants,
+// pointers) and a SpecCtl (the mutable control block the kernels update).
+// Kernels take an array of SpecDev plus a block->specimen table, so a single
+// launch advances one specimen or a whole batch of them: the block's
+// specimen is specs[b2s[blockIdx.x]] and its block index inside that
+// specimen is blockIdx.x - first block of that specimen.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pta.h"
+
+namespace pta {
+
+constexpr int TPB = 128;        // threads per block of the atom and pair kernels
+constexpr int CELL_WARPS = 8;   // warps per block of the cell-sort kernel
+constexpr int SCAN_THREADS = 1024;
+
+// grid quantum of the mixed-precision position split x = hi + lo:
+// hi is a multiple of 2^-12 A (exact in FP32 for |x| < 512 A), |lo| <= 2^-13 A
+constexpr double HI_SCALE = 4096.0;
+constexpr double HI_QUANTUM = 1.0 / 4096.0;
+constexpr double MIXED_RANGE = 511.0;
+
+enum Phase : int { PH_IDLE = 0, PH_REFRESH = 1, PH_RUN = 2 };
+enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4 };
+enum Mode : int { MODE_STEP = 0, MODE_EVAL = 1 };
+enum AtomFlag : uint8_t { FLAG_MOBILE = 0, FLAG_LEFT = 1, FLAG_RIGHT = 2 };
+
+// Sutton-Chen potential with the shifted-force cut, in both precisions.
+//   phi_k(r)  = s^k - A_k + B_k (r - rc),   s = a/r, A_k = (a/rc)^k, B_k = k A_k / rc
+//   phi_k'(r) = -k s^k / r + B_k
+struct PotDev {
+    double eps, c, a, rc, rc2, An, Bn, Am, Bm, ec;
+    int n, m;
+    float f_eps, f_a, f_rc, f_rc2, f_An, f_Bn, f_Am, f_Bm, f_ec, f_ec2h;
+    int sc76;  // 1 when (n, m) == (7, 6): the fast specialised kernels apply
+};
+
+// slow-variable record of the coarse-step logic (FP64)
+struct PtaDev {
+    double v[3], R_t[3], R_tmD[3], R_tmh[3];
+    double R3[3][3];  // means of the last three bursts, by slot
+    double t;
+    int has_tmh, init, jump[3], pad;
+};
+
+struct SpecCtl {
+    int phase;       // Phase
+    int parity;      // which position buffer is current
+    int rebuild;     // 1: build the neighbour list before the next pair pass
+    int err;         // sticky ErrBit mask
+    long long nsteps, done;
+    unsigned int blocks_done;  // last-block counter of the force kernel
+    int list_L;                // lanes the current list layout was built for
+    int rebuilds;              // list builds in the current burst
+    int max_nn;                // largest neighbour count at the last build
+    double sum[3];             // running sums of K, U, T over the burst
+    double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
+    double mb[8];              // scratch of the Maxwell-Boltzmann set-up
+    pta_averages last;         // averages of the last finished burst
+    PtaDev pta;
+};
+
+struct SpecDev {
+    // sizes
+    int n, L, prec, axis, cap;
+    int blk_pair0, nblk_pair;  // pair kernels: TPB/L atoms per block
+    int blk_atom0, nblk_atom;  // one thread per atom
+    int blk_cell0, nblk_cell;  // one warp per cell
+    int spec_index;            // index of this specimen in the launch table
+    // lattice (creation only)
+    int ncl[3];
+    double a0, grip_width;
+    // cell grid
+    double org[3];
+    double hcell, inv_h;
+    int nc[3];
+    int ncell;
+    // list radius (rc + skin)^2 and its FP32 bracket; half skin squared
+    double rl2;
+    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h;
+    float f_org[3];
+    PotDev pot;
+    // integration constants
+    double mass, dt, acc_half, ke_fac, t_fac;
+    float f_acc_half, f_ke_fac, f_dt;
+    int block_steps;
+    // coarse-step constants (Table 1)
+    double pta_h, pta_Delta, tol_v[3], tol_j[3], floor_[3];
+    // arrays
+    void *pos[2];   // FP64: double4 {x,y,z,0};  MIXED: float4 hi {x,y,z,0}
+    float4 *lo[2];  // MIXED only: float4 lo {x,y,z,0}
+    void *posfp;    // FP64: double4 {x,y,z,F'(rho)};  MIXED: float4 {lo.xyz, F'(rho)}
+    void *vel;      // FP64: double4; MIXED: float4
+    uint8_t *flags;
+    float4 *ref;    // positions at the last list build (skin test)
+    int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
+    int *nlist, *nn;
+    double *part;       // per pair block: K, U, R, max displacement^2
+    double *series;     // series_cap x 3 samples of the current burst
+    long long series_cap;
+    double *eval_out;   // n x 4: F, pe (MODE_EVAL)
+    double *stage;      // n x 6 doubles: import/export staging
+    SpecCtl *ctl;
+};
+
+struct Group {
+    int prec, L, sc76;
+    const int *b2s;
+    int nblk;
+};
+
+// one launch table: the specimens and, per kernel kind, block->specimen maps
+struct Tab {
+    const SpecDev *specs;
+    int nspec;
+    const int *b2s_atom;
+    int nblk_atom;
+    const int *b2s_cell;
+    int nblk_cell;
+    int ngroups;
+    Group grp[8];
+};
+
+// neighbour-list word of neighbour k of atom a for L lanes per atom: atoms
+// are grouped 32/L per warp; for each iteration q = k / L the warp's 32
+// words are contiguous, lane (a % (32/L)) * L + k % L.
+__host__ __device__ __forceinline__ long long nl_base(int a, int L, int cap) {
+    const int G = 32 / L;
+    return (long long)(a / G) * (32LL * (cap / L)) + (a % G) * L;
+}
+__host__ __device__ __forceinline__ long long nl_index(int a, int k, int L, int cap) {
+    return nl_base(a, L, cap) + (long long)(k / L) * 32 + (k % L);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// creation and state exchange, single specimen (d = device SpecDev)
+void launch_create(const SpecDev &h, const SpecDev *d, double sigma_v, double kT, uint64_t seed,
+                   cudaStream_t st);
+void launch_import(const SpecDev &h, const SpecDev *d, cudaStream_t st);
+void launch_export(const SpecDev &h, const SpecDev *d, cudaStream_t st);
+// batched
+void launch_strain(const Tab &t, const double *du, cudaStream_t st);
+void launch_burst_begin(const Tab &t, const long long *nsteps, cudaStream_t st);
+void launch_burst_end(const Tab &t, int slot, pta_averages *out, cudaStream_t st);
+void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
+void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
+void launch_rebuild(const Tab &t, int force, cudaStream_t st);
+void launch_density(const Tab &t, int force, cudaStream_t st);
+void launch_force(const Tab &t, int mode, cudaStream_t st);
+
+}  // namespace pta

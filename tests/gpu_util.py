@@ -1,0 +1,30 @@
+"""Helpers shared by the GPU parity tests."""
+import numpy as np
+import pytest
+
+
+def gpu_package():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device (there is no CPU fallback)")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2603_07321_gb300 as P
+    return P
+
+
+def on_grid(x, bits=24):
+    """Round coordinates to multiples of 2^-bits A, so that both the FP64 and
+    the mixed (hi + lo) representation hold them exactly."""
+    s = float(2 ** bits)
+    return np.round(np.asarray(x) * s) / s
+
+
+def force_error(f, f_ref):
+    """max_i |F_i - F_ref_i| / rms_i |F_ref_i|"""
+    scale = np.sqrt(np.mean(np.sum(f_ref ** 2, axis=1)))
+    return np.max(np.linalg.norm(f - f_ref, axis=1)) / scale
+
+
+def sorted_rows(counts, lst):
+    return [sorted(lst[i, : counts[i]].tolist()) for i in range(len(counts))]
