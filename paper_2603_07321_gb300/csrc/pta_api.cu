@@ -375,13 +375,13 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < iters; ++i) {
-        if (timed) cudaEventRecord(r->ev[4 * i + 0], r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
         launch_rebuild(r->tab, 0, r->cap);
-        if (timed) cudaEventRecord(r->ev[4 * i + 1], r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
         launch_density(r->tab, 0, r->cap);
-        if (timed) cudaEventRecord(r->ev[4 * i + 2], r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 2], r->cap, cudaEventRecordExternal);
         launch_force(r->tab, MODE_STEP, r->cap);
-        if (timed) cudaEventRecord(r->ev[4 * i + 3], r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 3], r->cap, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(r->cap, &g);
     if (e != cudaSuccess) {

@@ -262,3 +262,22 @@ def test_invalid_arguments(P):
     with pytest.raises(P.PTAError):
         ctx.set_state(np.full((ctx.n, 3), np.nan), np.zeros((ctx.n, 3)))
     ctx.close()
+
+
+def test_kernel_timing_records_every_iteration(P, oracle):
+    ctx = P.Ctx((6, 6, 6), T0=300.0, seed=4, precision=P.PREC_MIXED)
+    ctx.fine_burst(10)
+    s_ref = ctx.series().copy()
+    ctx.set_timing(True)
+    ctx.fine_burst(100)
+    t = ctx.timing()
+    assert t.iterations == 101  # one force refresh + 100 steps
+    assert t.force_ms > 0 and t.density_ms > 0 and t.rebuild_ms > 0
+    ctx.set_timing(False)
+    # timing changes nothing in the results
+    ctx2 = P.Ctx((6, 6, 6), T0=300.0, seed=4, precision=P.PREC_MIXED)
+    ctx2.fine_burst(10)
+    ctx2.fine_burst(100)
+    assert np.array_equal(ctx.series(), ctx2.series())
+    ctx.close()
+    ctx2.close()
