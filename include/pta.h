@@ -62,7 +62,9 @@ typedef enum {
     PTA_ESTATE = -6,          /* the call is not valid in the context's state          */
     PTA_ERANGE = -7,          /* a coordinate left the range the mixed-precision
                                  representation holds (|x| < 512 A)                    */
-    PTA_EUNSUPPORTED = -8     /* an option this build does not provide                 */
+    PTA_EUNSUPPORTED = -8,    /* an option this build does not provide                 */
+    PTA_ECAPACITY = -9        /* the input exceeds the fixed scratch size of
+                                 pta_neighbours_noalloc                              */
 } pta_status;
 
 enum { PTA_POT_SUTTON_CHEN_SF = 1 };
@@ -266,6 +268,49 @@ int pta_batch_coarse_step(pta_batch *batch, pta_coarse_result *out);
 int pta_batch_tick(pta_batch *batch, pta_coarse_result *out);
 int pta_batch_set_timing(pta_batch *batch, int enable);
 int pta_batch_get_timing(pta_batch *batch, pta_kernel_times *out);
+
+/* Neighbour lists without device allocation.
+ *
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory, such as an application whose memory pool
+ * already holds the whole GPU, or a latency-critical loop in which
+ * cudaMalloc and cudaFree (which may synchronise the device) are not
+ * allowed.  It builds the same Verlet lists as the library's list build
+ * (every j != i with (dx*dx + dy*dy) + dz*dz < rlist^2 in FP64, candidates
+ * from a cell grid over [box_lo, box_hi] with atoms outside clamped onto
+ * its border cells) but allocates nothing: its scratch memory (cell counts
+ * and starts, the atoms' cells, the sorted cell contents) is a fixed array
+ * in the library, about 2.1 MB, that every GPU which loads the library holds
+ * until the process exits.
+ *
+ *   pos_dev     n x 3 doubles, atom-major, in device memory (read only)
+ *   n           1 .. PTA_NOALLOC_MAX_ATOMS atoms
+ *   box_lo/hi   host arrays of 3 doubles: the cell grid's extent (A)
+ *   rlist       list radius (A); the grid has at most PTA_NOALLOC_MAX_CELLS
+ *               cells of edge rlist (1 + 1e-4)
+ *   cap         row length of list_dev
+ *   counts_dev  n int32 in device memory: neighbour count of each atom
+ *               (at most cap)
+ *   list_dev    n x cap int32 in device memory, row-major: the neighbours
+ *               of atom i in cell order, then increasing index
+ *   max_count   host int: the largest count before truncation
+ *   stream      cudaStream_t to queue the work on; the call returns once
+ *               the work is done
+ * Returns PTA_ECAPACITY when n or the cell count exceeds the fixed scratch,
+ * PTA_ENEIGH_OVERFLOW when an atom had more than cap neighbours (rows are
+ * then truncated), PTA_EINVAL for bad arguments.
+ *
+ * Every call shares the one scratch array and clears what must start at
+ * zero; calls that overlap on the GPU (from two streams or two host
+ * threads) race on it and must be serialised by the caller.  The first
+ * call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. */
+#define PTA_NOALLOC_MAX_ATOMS 131072
+#define PTA_NOALLOC_MAX_CELLS 65536
+int pta_neighbours_noalloc(const double *pos_dev, int32_t n, const double box_lo[3],
+                           const double box_hi[3], double rlist, int32_t cap, int32_t *counts_dev,
+                           int32_t *list_dev, int32_t *max_count, void *stream);
 
 #ifdef __cplusplus
 }

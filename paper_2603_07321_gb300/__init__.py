@@ -38,7 +38,7 @@ SRC_PREDICTED, SRC_MEASURE_JUMP, SRC_MEASURE_MISMATCH = 0, 1, 2
 
 _STATUS = {0: "PTA_OK", -1: "PTA_EINVAL", -2: "PTA_ENOMEM", -3: "PTA_ECUDA",
            -4: "PTA_ENEIGH_OVERFLOW", -5: "PTA_ENAN", -6: "PTA_ESTATE", -7: "PTA_ERANGE",
-           -8: "PTA_EUNSUPPORTED"}
+           -8: "PTA_EUNSUPPORTED", -9: "PTA_ECAPACITY"}
 
 
 class PTAError(RuntimeError):
@@ -145,6 +145,10 @@ _SIGS = {
     "pta_get_timing": (ctypes.c_int, [_VP, _P(KernelTimes)]),
     "pta_batch_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pta_batch_get_timing": (ctypes.c_int, [_VP, _P(KernelTimes)]),
+    "pta_neighbours_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_double),
+                                              _P(ctypes.c_double), ctypes.c_double,
+                                              ctypes.c_int32, _VP, _VP, _P(ctypes.c_int32),
+                                              _VP]),
 }
 
 _lib = None
@@ -399,6 +403,30 @@ def pta_batch_get_timing(b) -> KernelTimes:
     t = KernelTimes()
     _check(load().pta_batch_get_timing(b, ctypes.byref(t)), "pta_batch_get_timing")
     return t
+
+
+NOALLOC_MAX_ATOMS = 131072
+NOALLOC_MAX_CELLS = 65536
+
+
+def pta_neighbours_noalloc(pos_dev_ptr: int, n: int, box_lo, box_hi, rlist: float, cap: int,
+                           counts_dev_ptr: int, list_dev_ptr: int, stream=None) -> int:
+    """Neighbour lists from device positions into caller-owned device
+    arrays, for callers that cannot allocate device memory (the library
+    uses a fixed scratch array instead).  Pointers are device addresses
+    (e.g. tensor.data_ptr()); returns the largest neighbour count.  Calls
+    share the scratch array and must not overlap on the GPU."""
+    lo = (ctypes.c_double * 3)(*[float(x) for x in box_lo])
+    hi = (ctypes.c_double * 3)(*[float(x) for x in box_hi])
+    mx = ctypes.c_int32()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().pta_neighbours_noalloc(_VP(pos_dev_ptr), int(n), lo, hi, float(rlist), int(cap),
+                                         _VP(counts_dev_ptr), _VP(list_dev_ptr),
+                                         ctypes.byref(mx), _VP(stream)),
+           "pta_neighbours_noalloc")
+    return mx.value
 
 
 # ---------------------------------------------------------------------------

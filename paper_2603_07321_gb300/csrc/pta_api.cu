@@ -721,6 +721,7 @@ const char *pta_strerror(int s) {
         case PTA_ESTATE: return "call not valid in this state";
         case PTA_ERANGE: return "coordinate outside the mixed-precision range";
         case PTA_EUNSUPPORTED: return "unsupported option";
+        case PTA_ECAPACITY: return "input exceeds the fixed scratch of the no-allocation entry point";
         default: return "unknown status";
     }
 }
