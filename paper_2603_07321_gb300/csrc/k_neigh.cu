@@ -5,9 +5,12 @@
 // contraction.  Candidates come from the 27 cells around i's cell on a grid
 // of edge >= rc + skin; atoms outside the grid are clamped onto its border
 // cells, which keeps every pair within reach (clamping is non-expansive).
-// Cells are visited in increasing linear index and each cell's atoms in
-// increasing atom index, so a list's order depends only on the grid and the
-// positions: builds are deterministic.
+// After binning, the atoms themselves are permuted into cell order (cells in
+// increasing linear index, atoms of a cell in their previous order), so that
+// the 32 atoms of a warp share a cell and read overlapping neighbours, and a
+// cell's atoms are one contiguous range.  The list order (cell order, then
+// slot) is therefore a function of positions and grid: builds are
+// deterministic.  orig[] keeps each slot's creation-order index.
 //
 // The list is rebuilt only when the force kernel found an atom that moved
 // more than skin/2 since the last build (or on request); every kernel here
@@ -134,6 +137,52 @@ __global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__rest
     if (lane == 0) S.cell_cnt[c] = 0;
 }
 
+// sort the per-atom state into cell order: gather into scratch, then copy back
+__global__ void k_permute_gather(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                                 int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int p = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (p >= S.n) return;
+    const int src = S.cell_atoms[p];
+    const int par = S.ctl->parity;
+    const PermLayout Lo = perm_layout(S.n, S.prec);
+    char *t = (char *)S.perm_tmp;
+    if (S.prec == PTA_PREC_FP64) {
+        ((double4_32a *)(t + Lo.pos))[p] = ((const double4_32a *)S.pos[par])[src];
+        ((double4_32a *)(t + Lo.vel))[p] = ((const double4_32a *)S.vel)[src];
+    } else {
+        ((float4 *)(t + Lo.pos))[p] = ((const float4 *)S.pos[par])[src];
+        ((float4 *)(t + Lo.lo))[p] = S.lo[par][src];
+        ((float4 *)(t + Lo.vel))[p] = ((const float4 *)S.vel)[src];
+    }
+    ((uint8_t *)(t + Lo.flags))[p] = S.flags[src];
+    ((int *)(t + Lo.orig))[p] = S.orig[src];
+    ((int *)(t + Lo.cell))[p] = S.atom_cell[src];
+}
+
+__global__ void k_permute_scatter(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                                  int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!build_active(S, force)) return;
+    const int p = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (p >= S.n) return;
+    const int par = S.ctl->parity;
+    const PermLayout Lo = perm_layout(S.n, S.prec);
+    const char *t = (const char *)S.perm_tmp;
+    if (S.prec == PTA_PREC_FP64) {
+        ((double4_32a *)S.pos[par])[p] = ((const double4_32a *)(t + Lo.pos))[p];
+        ((double4_32a *)S.vel)[p] = ((const double4_32a *)(t + Lo.vel))[p];
+    } else {
+        ((float4 *)S.pos[par])[p] = ((const float4 *)(t + Lo.pos))[p];
+        S.lo[par][p] = ((const float4 *)(t + Lo.lo))[p];
+        ((float4 *)S.vel)[p] = ((const float4 *)(t + Lo.vel))[p];
+    }
+    S.flags[p] = ((const uint8_t *)(t + Lo.flags))[p];
+    S.orig[p] = ((const int *)(t + Lo.orig))[p];
+    S.atom_cell[p] = ((const int *)(t + Lo.cell))[p];
+}
+
 // one thread per atom: scan the 27 cells around the atom's cell
 __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs,
                                                const int *__restrict__ b2s, int force) {
@@ -166,8 +215,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                     if (x < 0 || x >= S.nc[0]) continue;
                     const int cc = x + S.nc[0] * (y + S.nc[1] * z);
                     const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
-                    for (int p = s; p < e; ++p) {
-                        const int j = S.cell_atoms[p];
+                    for (int j = s; j < e; ++j) {
                         if (j == a) continue;
                         bool in;
                         if (mixed) {
@@ -201,7 +249,9 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                             in = r2 < S.rl2;
                         }
                         if (in) {
-                            if (cnt < S.cap) S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] = j;
+                            if (cnt < S.cap)
+                                S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
+                                    j | (((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << NL_JBITS);
                             ++cnt;
                         }
                     }
@@ -210,6 +260,12 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         }
         S.nn[a] = cnt < S.cap ? cnt : S.cap;
         S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
+        if (mixed) {
+            // the neighbour-visible record relative to the (new) cell centre
+            const float3 C = cell_centre(S, c);
+            S.rel[par][a] = make_float4((ha.x - C.x) + la.x, (ha.y - C.y) + la.y,
+                                        (ha.z - C.z) + la.z, 0.f);
+        }
     }
     // block maximum of the counts, one atomic per block
     __shared__ int smax[TPB / 32];
@@ -246,6 +302,8 @@ void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_scan<<<t.nspec, SCAN_THREADS, 0, st>>>(t.specs, force);
     k_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_cell_sort<<<t.nblk_cell, CELL_WARPS * 32, 0, st>>>(t.specs, t.b2s_cell, force);
+    k_permute_gather<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_permute_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);
 }

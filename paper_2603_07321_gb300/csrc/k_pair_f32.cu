@@ -1,9 +1,12 @@
 // Mixed-precision pair kernels: Sutton-Chen EAM density and forces in FP32
-// on relative coordinates, positions kept as an exact FP32 pair x = hi + lo
-// (hi on a 2^-12 A grid, |lo| <= 2^-13 A), so that
-//     r_j - r_i = (hi_j - hi_i) + (lo_j - lo_i)
-// is formed with the first difference exact; velocities FP32; energies,
-// stresses and time averages reduced in FP64.
+// on relative coordinates.  Positions are kept as an exact FP32 pair
+// x = hi + lo (hi on a 2^-12 A grid, |lo| <= 2^-13 A) for the integration;
+// what a neighbour reads is one 16-byte record, the position relative to the
+// centre of its cell, rel = (hi - C) + lo, so that with the cell offset d
+// coded in the list entry
+//     r_j - r_i = (rel_j - rel_i) + h d
+// (C and h on exact grids).  Velocities FP32; energies, stresses and time
+// averages reduced in FP64.
 //
 // Pass 1 (density): rho_i = sum_j phi_m(r_ij), then B'(rho_i) =
 // -eps c / (2 sqrt(rho_i)) stored beside lo_i.  Eq. (pe).
@@ -46,7 +49,7 @@ struct PowF {
 };
 
 template <int L, bool SC76>
-__global__ void __launch_bounds__(TPB) k_density_f32(const SpecDev *__restrict__ specs,
+__global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restrict__ specs,
                                                      const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     const SpecCtl *ctl = S.ctl;
@@ -56,25 +59,32 @@ __global__ void __launch_bounds__(TPB) k_density_f32(const SpecDev *__restrict__
     const int a = (blockIdx.x - S.blk_pair0) * APB + threadIdx.x / L;
     const int l = threadIdx.x % L;
     const bool valid = a < S.n;
-    const float4 *__restrict__ hi = (const float4 *)S.pos[par];
-    const float4 *__restrict__ lo = S.lo[par];
+    const float4 *__restrict__ rel = S.rel[par];
     const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, Am = S.pot.f_Am, Bm = S.pot.f_Bm,
-                rc = S.pot.f_rc;
+                rc = S.pot.f_rc, h = S.f_h;
     const int m = S.pot.m;
     float rho = 0.f;
-    float4 hia = make_float4(0, 0, 0, 0), loa = hia;
+    float4 ra = make_float4(0, 0, 0, 0);
     if (valid) {
-        hia = hi[a];
-        loa = lo[a];
+        ra = rel[a];
         const int nn = S.nn[a];
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
-        for (int k = l; k < nn; k += L) {
-            const int j = __ldg(lst + (k / L) * 32 + (k % L));
-            const float4 hj = __ldg(hi + j);
-            const float4 lj = __ldg(lo + j);
-            const float dx = (hj.x - hia.x) + (lj.x - loa.x);
-            const float dy = (hj.y - hia.y) + (lj.y - loa.y);
-            const float dz = (hj.z - hia.z) + (lj.z - loa.z);
+        // software pipeline: entry two iterations ahead, record one ahead
+        // (a slot past the end reads the atom itself, always in bounds)
+        int q = 0;  // iteration: neighbour k = q * L + l
+        int e1 = (l < nn) ? __ldg(lst + l) : a;
+        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a;
+        float4 rn = __ldg(rel + (e1 & NL_JMASK));
+        for (int k = l; k < nn; k += L, ++q) {
+            const float4 rj = rn;
+            const unsigned code = (unsigned)e1 >> NL_JBITS;
+            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a;
+            rn = __ldg(rel + (e2 & NL_JMASK));
+            e1 = e2;
+            e2 = e3;
+            const float dx = fmaf(nl_off(code), h, rj.x - ra.x);
+            const float dy = fmaf(nl_off(code >> 2), h, rj.y - ra.y);
+            const float dz = fmaf(nl_off(code >> 4), h, rj.z - ra.z);
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < rc2) {
                 const float ir = rsqrtf(r2);
@@ -87,12 +97,12 @@ __global__ void __launch_bounds__(TPB) k_density_f32(const SpecDev *__restrict__
     rho = lane_sum<L>(rho);
     if (valid && l == 0) {
         const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
-        ((float4 *)S.posfp)[a] = make_float4(loa.x, loa.y, loa.z, fp);
+        ((float4 *)S.posfp)[a] = make_float4(ra.x, ra.y, ra.z, fp);
     }
 }
 
 template <int L, bool SC76>
-__global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ specs,
+__global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict__ specs,
                                                    const int *__restrict__ b2s, int mode) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     SpecCtl *ctl = S.ctl;
@@ -105,26 +115,31 @@ __global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ s
     const int a = lb * APB + threadIdx.x / L;
     const int l = threadIdx.x % L;
     const bool valid = a < S.n;
-    const float4 *__restrict__ hi = (const float4 *)S.pos[par];
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
-    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, rc = S.pot.f_rc;
+    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, rc = S.pot.f_rc, h = S.f_h;
     const float An = S.pot.f_An, Bn = S.pot.f_Bn, Bm = S.pot.f_Bm, eps = S.pot.f_eps;
     const int n = S.pot.n, m = S.pot.m;
     const float fn = (float)n, fm = (float)m;
     float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f;
-    float4 hia = make_float4(0, 0, 0, 0), lfa = hia;
+    float4 lfa = make_float4(0, 0, 0, 0);
     if (valid) {
-        hia = hi[a];
         lfa = lf[a];
         const int nn = S.nn[a];
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
-        for (int k = l; k < nn; k += L) {
-            const int j = __ldg(lst + (k / L) * 32 + (k % L));
-            const float4 hj = __ldg(hi + j);
-            const float4 lj = __ldg(lf + j);
-            const float dx = (hj.x - hia.x) + (lj.x - lfa.x);
-            const float dy = (hj.y - hia.y) + (lj.y - lfa.y);
-            const float dz = (hj.z - hia.z) + (lj.z - lfa.z);
+        int q = 0;
+        int e1 = (l < nn) ? __ldg(lst + l) : a;
+        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a;
+        float4 rn = __ldg(lf + (e1 & NL_JMASK));
+        for (int k = l; k < nn; k += L, ++q) {
+            const float4 lj = rn;
+            const unsigned code = (unsigned)e1 >> NL_JBITS;
+            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a;
+            rn = __ldg(lf + (e2 & NL_JMASK));
+            e1 = e2;
+            e2 = e3;
+            const float dx = fmaf(nl_off(code), h, lj.x - lfa.x);
+            const float dy = fmaf(nl_off(code >> 2), h, lj.y - lfa.y);
+            const float dz = fmaf(nl_off(code >> 4), h, lj.z - lfa.z);
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < rc2) {
                 const float ir = rsqrtf(r2);
@@ -156,7 +171,7 @@ __global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ s
         if (mode == MODE_EVAL) {
             ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
             double4_32a *o = (double4_32a *)S.eval_out;
-            o[a] = make_double4_32a(fx, fy, fz, pe);
+            o[S.orig[a]] = make_double4_32a(fx, fy, fz, pe);
         } else {
             const float kh = S.f_acc_half;
             if (phase == PH_RUN) {
@@ -167,7 +182,9 @@ __global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ s
                 }
                 ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
-            float h[3] = {hia.x, hia.y, hia.z}, q[3] = {lfa.x, lfa.y, lfa.z};
+            const float4 hia = ((const float4 *)S.pos[par])[a];
+            const float4 loa = S.lo[par][a];
+            float h[3] = {hia.x, hia.y, hia.z}, q[3] = {loa.x, loa.y, loa.z};
             const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
             if (start && flag == FLAG_MOBILE) {
                 v.x += fx * kh;
@@ -190,6 +207,9 @@ __global__ void __launch_bounds__(TPB) k_force_f32(const SpecDev *__restrict__ s
             }
             ((float4 *)S.pos[par ^ 1])[a] = make_float4(h[0], h[1], h[2], 0.f);
             S.lo[par ^ 1][a] = make_float4(q[0], q[1], q[2], 0.f);
+            const float3 C = cell_centre(S, S.atom_cell[a]);
+            S.rel[par ^ 1][a] = make_float4((h[0] - C.x) + q[0], (h[1] - C.y) + q[1],
+                                            (h[2] - C.z) + q[2], 0.f);
             ((float4 *)S.vel)[a] = v;
             const float4 rf = S.ref[a];
             const float ex = (h[0] - rf.x) + q[0], ey = (h[1] - rf.y) + q[1],

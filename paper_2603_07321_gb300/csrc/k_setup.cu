@@ -86,6 +86,7 @@ __global__ void k_lattice(const SpecDev *__restrict__ sp) {
     S.stage[3 * (size_t)a + 0] = p[0];
     S.stage[3 * (size_t)a + 1] = p[1];
     S.stage[3 * (size_t)a + 2] = p[2];
+    S.orig[a] = a;
     // grips: lowest coordinate along the axis is 0, highest a0 (n - 1/2)
     const double lo = 0.0;
     const double hi = S.a0 * ((double)(S.ncl[S.axis] - 1) + 0.5);
@@ -205,8 +206,9 @@ __global__ void k_import(const SpecDev *__restrict__ sp) {
     const int a = blockIdx.x * TPB + threadIdx.x;
     if (a >= S.n) return;
     const int par = S.ctl->parity;
-    const double *p = S.stage + 3 * (size_t)a;
-    const double *v = S.stage + 3 * (size_t)S.n + 3 * (size_t)a;
+    const size_t o = (size_t)S.orig[a];  // stage is in creation order
+    const double *p = S.stage + 3 * o;
+    const double *v = S.stage + 3 * (size_t)S.n + 3 * o;
     if (S.prec == PTA_PREC_FP64) {
         ((double4_32a *)S.pos[par])[a] = make_double4_32a(p[0], p[1], p[2], 0.0);
         ((double4_32a *)S.vel)[a] = make_double4_32a(v[0], v[1], v[2], 0.0);
@@ -227,8 +229,9 @@ __global__ void k_export(const SpecDev *__restrict__ sp) {
     const int a = blockIdx.x * TPB + threadIdx.x;
     if (a >= S.n) return;
     const int par = S.ctl->parity;
-    double *p = S.stage + 3 * (size_t)a;
-    double *v = S.stage + 3 * (size_t)S.n + 3 * (size_t)a;
+    const size_t o = (size_t)S.orig[a];  // stage is in creation order
+    double *p = S.stage + 3 * o;
+    double *v = S.stage + 3 * (size_t)S.n + 3 * o;
     if (S.prec == PTA_PREC_FP64) {
         const double4_32a q = ((const double4_32a *)S.pos[par])[a];
         const double4_32a w = ((const double4_32a *)S.vel)[a];

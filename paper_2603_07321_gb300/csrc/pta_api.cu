@@ -275,7 +275,9 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     }
     z->nblk_pair = (int)((z->n * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
-    z->h = rl * (1.0 + 1e-4);
+    // cell edge a multiple of 2^-11 A and grid origin on the 2^-12 A grid, so
+    // that cell centres and centre differences are exact in FP32
+    z->h = std::ceil(rl * (1.0 + 1e-4) * 2048.0) / 2048.0;
     double maxspan = 0;
     double span[3];
     for (int d = 0; d < 3; ++d) {
@@ -285,7 +287,7 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     const double margin = 0.25 * maxspan + 2.0 * z->h;
     long long ncell = 1;
     for (int d = 0; d < 3; ++d) {
-        z->org[d] = -margin;
+        z->org[d] = std::floor(-margin * 4096.0) / 4096.0;
         z->nc[d] = (int)std::floor((span[d] + 2.0 * margin) / z->h) + 1;
         ncell *= z->nc[d];
     }
@@ -308,6 +310,8 @@ static size_t footprint(const Sizes &z, int prec) {
     if (prec != PTA_PREC_FP64) {
         add(16 * n);
         add(16 * n);                 // lo[2]
+        add(16 * n);
+        add(16 * n);                 // rel[2]
     }
     add(p * n);                      // posfp
     add(p * n);                      // vel
@@ -318,6 +322,8 @@ static size_t footprint(const Sizes &z, int prec) {
     add(4 * ((size_t)z.ncell + 1));  // cell_start
     add(4 * n);                      // cell_tmp
     add(4 * n);                      // cell_atoms
+    add(4 * n);                      // orig
+    add(perm_layout(n, prec).total); // permutation scratch
     add(4 * z.list_words);           // nlist
     add(4 * n);                      // nn
     add(32 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
@@ -797,6 +803,8 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     if (!f64) {
         AL(lo[0], 16 * n, float4 *);
         AL(lo[1], 16 * n, float4 *);
+        AL(rel[0], 16 * n, float4 *);
+        AL(rel[1], 16 * n, float4 *);
     }
     AL(posfp, p * n, void *);
     AL(vel, p * n, void *);
@@ -807,6 +815,8 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     AL(cell_start, 4 * ((size_t)z.ncell + 1), int *);
     AL(cell_tmp, 4 * n, int *);
     AL(cell_atoms, 4 * n, int *);
+    AL(orig, 4 * n, int *);
+    AL(perm_tmp, perm_layout(n, c->par.precision).total, void *);
     AL(nlist, 4 * z.list_words, int *);
     AL(nn, 4 * n, int *);
     AL(part, 32 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
@@ -867,6 +877,7 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.hcell = z.h;
     s.inv_h = 1.0 / z.h;
     s.f_inv_h = (float)s.inv_h;
+    s.f_h = (float)z.h;
     s.ncell = z.ncell;
     const double rl = c->pot.rc + c->par.skin;
     s.rl2 = rl * rl;
@@ -939,11 +950,23 @@ int pta_natoms(const pta_ctx *c, int64_t *n) {
     return PTA_OK;
 }
 
+// creation-order index of every slot (atoms are kept sorted by cell)
+static int fetch_orig(pta_ctx *c, std::vector<int> &orig) {
+    orig.resize((size_t)c->hd.n);
+    CK(cudaMemcpyAsync(orig.data(), c->hd.orig, 4 * (size_t)c->hd.n, cudaMemcpyDeviceToHost,
+                       c->stream));
+    return PTA_OK;
+}
+
 int pta_get_flags(pta_ctx *c, uint8_t *flags, int64_t n) {
     if (!c || !flags || n != c->hd.n) return PTA_EINVAL;
     if (c->broken) return PTA_ECUDA;
-    CK(cudaMemcpyAsync(flags, c->hd.flags, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<uint8_t> f((size_t)n);
+    std::vector<int> orig;
+    CK(cudaMemcpyAsync(f.data(), c->hd.flags, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CKR(fetch_orig(c, orig));
     CK(cudaStreamSynchronize(c->stream));
+    for (int64_t p = 0; p < n; ++p) flags[orig[p]] = f[p];
     return PTA_OK;
 }
 
@@ -1081,16 +1104,20 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     const long long G = 32 / s.L;
     const size_t words = (size_t)((n + G - 1) / G) * G * s.cap;
     raw.resize(words);
+    std::vector<int> orig;
     CK(cudaMemcpyAsync(raw.data(), s.nlist, 4 * words, cudaMemcpyDeviceToHost, c->stream));
+    CKR(fetch_orig(c, orig));
     CK(cudaStreamSynchronize(c->stream));
     *max_count = ctl.max_nn;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
     if (ctl.max_nn > cap) return PTA_EINVAL;
     for (int64_t a = 0; a < n; ++a) {
-        if (counts) counts[a] = nn[a];
+        const int64_t o = orig[a];
+        if (counts) counts[o] = nn[a];
         if (list)
             for (int k = 0; k < nn[a]; ++k)
-                list[a * (int64_t)cap + k] = raw[(size_t)nl_index((int)a, k, s.L, s.cap)];
+                list[o * (int64_t)cap + k] =
+                    orig[raw[(size_t)nl_index((int)a, k, s.L, s.cap)] & NL_JMASK];
     }
     return PTA_OK;
 }
@@ -1108,7 +1135,7 @@ struct CkptHeader {
 static size_t ckpt_payload(const pta_ctx *c) {
     const size_t n = (size_t)c->hd.n;
     const size_t p = (c->hd.prec == PTA_PREC_FP64) ? 32 : 16;
-    return p * n * 2 + (c->hd.prec == PTA_PREC_FP64 ? 0 : 16 * n);
+    return p * n * 2 + (c->hd.prec == PTA_PREC_FP64 ? 0 : 16 * n) + n + 4 * n;
 }
 
 int pta_save_state(pta_ctx *c, void *buf, size_t *len) {
@@ -1143,8 +1170,13 @@ int pta_save_state(pta_ctx *c, void *buf, size_t *len) {
     o += p * n;
     CK(cudaMemcpyAsync(o, c->hd.vel, p * n, cudaMemcpyDeviceToHost, c->stream));
     o += p * n;
-    if (c->hd.prec != PTA_PREC_FP64)
+    if (c->hd.prec != PTA_PREC_FP64) {
         CK(cudaMemcpyAsync(o, c->hd.lo[par], 16 * n, cudaMemcpyDeviceToHost, c->stream));
+        o += 16 * n;
+    }
+    CK(cudaMemcpyAsync(o, c->hd.flags, n, cudaMemcpyDeviceToHost, c->stream));
+    o += n;
+    CK(cudaMemcpyAsync(o, c->hd.orig, 4 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *len = need;
     return PTA_OK;
@@ -1176,8 +1208,13 @@ int pta_load_state(pta_ctx *c, const void *buf, size_t len) {
     o += p * n;
     CK(cudaMemcpyAsync(c->hd.vel, o, p * n, cudaMemcpyHostToDevice, c->stream));
     o += p * n;
-    if (c->hd.prec != PTA_PREC_FP64)
+    if (c->hd.prec != PTA_PREC_FP64) {
         CK(cudaMemcpyAsync(c->hd.lo[par], o, 16 * n, cudaMemcpyHostToDevice, c->stream));
+        o += 16 * n;
+    }
+    CK(cudaMemcpyAsync(c->hd.flags, o, n, cudaMemcpyHostToDevice, c->stream));
+    o += n;
+    CK(cudaMemcpyAsync(c->hd.orig, o, 4 * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->hd.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->u = h.u;

@@ -82,7 +82,7 @@ struct SpecDev {
     int ncell;
     // list radius (rc + skin)^2 and its FP32 bracket; half skin squared
     double rl2;
-    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h;
+    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h, f_h;
     float f_org[3];
     PotDev pot;
     // integration constants
@@ -94,11 +94,15 @@ struct SpecDev {
     // arrays
     void *pos[2];   // FP64: double4 {x,y,z,0};  MIXED: float4 hi {x,y,z,0}
     float4 *lo[2];  // MIXED only: float4 lo {x,y,z,0}
-    void *posfp;    // FP64: double4 {x,y,z,F'(rho)};  MIXED: float4 {lo.xyz, F'(rho)}
+    void *posfp;    // FP64: double4 {x,y,z,F'(rho)};  MIXED: float4 {rel.xyz, F'(rho)}
+    float4 *rel[2]; // MIXED only: position relative to the centre of its cell (FP32):
+                    // the 16-byte record the pair passes read for a neighbour
     void *vel;      // FP64: double4; MIXED: float4
     uint8_t *flags;
     float4 *ref;    // positions at the last list build (skin test)
     int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
+    int *orig;        // original index (creation order) of the atom stored at each slot
+    void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
     int *nlist, *nn;
     double *part;       // per pair block: K, U, R, max displacement^2
     double *series;     // series_cap x 3 samples of the current burst
@@ -125,6 +129,52 @@ struct Tab {
     int ngroups;
     Group grp[8];
 };
+
+// Verlet-list entry: neighbour index in the low 26 bits, the neighbour's
+// cell offset (dx, dy, dz) in {-1, 0, 1}^3 relative to the atom's cell in
+// the high 6 bits as (dx+1) | (dy+1) << 2 | (dz+1) << 4.  With cell centres
+// and the cell edge h on exact grids, r_j - r_i = (rel_j - rel_i) + h * d.
+constexpr int NL_JBITS = 26;
+constexpr int NL_JMASK = (1 << NL_JBITS) - 1;
+
+// FP32 value (code & 3) - 1 in {-1, 0, 1}, without an integer conversion:
+// 0x4B400000 is 1.5 * 2^23, whose last mantissa bits take small integers exactly
+__device__ __forceinline__ float nl_off(unsigned bits) {
+    return __int_as_float(0x4B400000 | (int)(bits & 3u)) - 12582913.0f;
+}
+
+// centre of cell c (exact in FP32: org on a 2^-12 grid, h a multiple of 2^-11)
+__device__ __forceinline__ float3 cell_centre(const SpecDev &S, int c) {
+    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
+    return make_float3(S.f_org[0] + ((float)cx + 0.5f) * S.f_h,
+                       S.f_org[1] + ((float)cy + 0.5f) * S.f_h,
+                       S.f_org[2] + ((float)cz + 0.5f) * S.f_h);
+}
+
+// segments of the permutation scratch (see perm_layout)
+struct PermLayout {
+    size_t pos, lo, vel, flags, orig, cell, total;
+};
+__host__ __device__ inline size_t perm_round(size_t x) { return (x + 255) / 256 * 256; }
+__host__ __device__ inline PermLayout perm_layout(size_t n, int prec) {
+    const size_t P = prec == PTA_PREC_FP64 ? 32 : 16;
+    PermLayout L;
+    size_t o = 0;
+    L.pos = o;
+    o += perm_round(P * n);
+    L.lo = o;
+    o += prec == PTA_PREC_FP64 ? 0 : perm_round(16 * n);
+    L.vel = o;
+    o += perm_round(P * n);
+    L.flags = o;
+    o += perm_round(n);
+    L.orig = o;
+    o += perm_round(4 * n);
+    L.cell = o;
+    o += perm_round(4 * n);
+    L.total = o;
+    return L;
+}
 
 // neighbour-list word of neighbour k of atom a for L lanes per atom: atoms
 // are grouped 32/L per warp; for each iteration q = k / L the warp's 32
