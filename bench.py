@@ -8,7 +8,7 @@ FP64 accumulators) and the coarse-step update.  The metric is atom-steps/s
 (atoms x fine steps per second), whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pta|reference]
-                    [--workload large|plain|batched|uneven]
+                    [--workload large|plain|batched|uneven|served]
 
 Under torchrun (N > 1) every rank advances its own specimen (independent
 replicas, no collective on the data path); the time is the maximum over
@@ -53,6 +53,13 @@ WORKLOADS = {
                          "10/100/300 K, half tension half compression, rates log-uniform "
                          "1e-4..1e-3/s, 3 bursts x 2,000 steps per coarse step, one launch "
                          "set per fine step for all replicas"),
+    "served": dict(name="served_poisson_16req", n_cells=None, T0=None, rate=None, burst=2000,
+                   precision=1, count=16,
+                   desc="first 16 requests of a Poisson trace (mean 2/s): cube side uniform "
+                        "10..49 cells, T0 in 10/100/300 K, rate log-uniform 1e-4..1e-3/s, "
+                        "tension or compression p=0.5, target strain 0.05..0.15, admitted by "
+                        "memory footprint; one bench step = one tick (a coarse step of every "
+                        "live specimen, 3 x 2,000 fine steps)"),
     "uneven": dict(name="uneven_28x_n10_49", n_cells=None, T0=300.0, rate=None, burst=2000,
                    precision=1, count=28,
                    desc="4 cubes each of 10,15,20,25,30,40,49 cells (3,786,384 atoms), "
@@ -158,18 +165,102 @@ def _dist():
     return ws, rank, local
 
 
-def _requests(wl, rank):
+def rank_requests(wl, rank):
+    """The specimens one rank advances: every rank runs the whole workload
+    on its own replicas (distinct seeds), so per-GPU work is fixed."""
     if wl["name"].startswith("batched"):
-        return PI.config_batched(64, 20)
-    if wl["name"].startswith("uneven"):
-        return PI.config_uneven()
-    return [PI.SpecimenRequest(n_cells=wl["n_cells"], T0=wl["T0"], seed=1 + rank,
-                               strain_rate=wl["rate"], burst_steps=wl["burst"])]
+        reqs = PI.config_batched(64, 20)
+    elif wl["name"].startswith("uneven"):
+        reqs = PI.config_uneven()
+    else:
+        reqs = [PI.SpecimenRequest(n_cells=wl["n_cells"], T0=wl["T0"], seed=1,
+                                   strain_rate=wl["rate"], burst_steps=wl["burst"])]
+    for r in reqs:
+        r.seed = r.seed + 100000 * rank
+    return reqs
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Maximum of x over the ranks of the default process group (x itself
+    without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
 # own arm
 # ---------------------------------------------------------------------------
+def run_served(args, wl):
+    """Served workload: the request loop of paper_2603_07321_gb300.serve on a
+    Poisson trace; a bench step is one tick of the server."""
+    import torch
+    import paper_2603_07321_gb300 as P
+    from paper_2603_07321_gb300.serve import GPUEngine, Request, Scheduler
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    P.build()
+    trace = PI.served_trace(16, seed=7 + rank)
+    reqs = [Request(rid=i, n_cells=r.n_cells, T0=r.T0, seed=r.seed, strain_rate=r.strain_rate,
+                    target_strain=r.target_strain, arrival_s=r.arrival_s,
+                    burst_steps=r.burst_steps, precision=wl["precision"])
+            for i, r in enumerate(trace)]
+    eng = GPUEngine()
+    free, _ = torch.cuda.mem_get_info()
+    sched = Scheduler(eng, mem_budget_bytes=int(0.8 * free), max_slots=64)
+    for r in reqs:
+        r.arrival_s = 0.0   # the trace is replayed as fast as the device allows
+        sched.submit(r)
+    for _ in range(args.warmup):
+        sched.tick()
+    torch.cuda.synchronize()
+    steps0 = sum(s["result"].atom_steps for s in sched.live.values()) + \
+        sum(r.atom_steps for r in sched.results.values())
+    lat0 = {rid: len(s["result"].tick_latency_s) for rid, s in sched.live.items()}
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sched.tick()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, "cuda")
+    clocks = sampler.stop()
+    steps1 = sum(s["result"].atom_steps for s in sched.live.values()) + \
+        sum(r.atom_steps for r in sched.results.values())
+    lat = [x for rid, s in sched.live.items() for x in s["result"].tick_latency_s[lat0.get(rid, 0):]]
+    natoms = sum(s["req"].n_cells ** 3 * 4 for s in sched.live.values())
+    # coarse steps each request needs to reach its target, at the measured tick time
+    need = [max(1, int(np.ceil(r.target_strain / (abs(r.strain_rate) * 1.0)))) + 1 for r in reqs]
+    tick = float(np.median(lat)) if lat else None
+    out = None
+    if rank == 0:
+        value = (steps1 - steps0) * ws / dt
+        out = {"metric": "atom-steps/s", "value": value, "unit": "atom-steps/s", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32", "data": "synthetic (seeded Poisson request trace)",
+               "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
+                          "live_specimens": len(sched.live), "parallelism": "continuous batching"},
+               "served": {"coarse_step_latency_s": {"p50": tick,
+                                                    "p99": float(np.percentile(lat, 99))
+                                                    if lat else None},
+                          "curve_latency_s_projected": {
+                              "p50": float(np.percentile(need, 50)) * tick if tick else None,
+                              "p99": float(np.percentile(need, 99)) * tick if tick else None,
+                              "note": "coarse steps to the target strain x median tick time"}},
+               "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    eng.close()
+    for s in list(sched.live.values()):
+        s["handle"].close()
+    return out
+
+
 def run_pta(args, wl):
     import torch
     import paper_2603_07321_gb300 as P
@@ -180,7 +271,7 @@ def run_pta(args, wl):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     P.build()
-    reqs = _requests(wl, rank)
+    reqs = rank_requests(wl, rank)
     ctxs = []
     for r in reqs:
         ctxs.append(P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=wl["precision"],
@@ -219,12 +310,7 @@ def run_pta(args, wl):
     ms = e0.elapsed_time(e1)
     kt = stepper.timing()
     stepper.set_timing(False)
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, "cuda")
     fine_per_step = 3 * max(r.burst_steps for r in reqs)
     atom_steps_rank = sum(c.n * 3 * r.burst_steps for c, r in zip(ctxs, reqs)) * args.steps
     value = atom_steps_rank * ws / (t_max / 1e3)
@@ -269,12 +355,7 @@ def run_pta(args, wl):
             hpos[:] = p
             hvel[:] = v
         barrier()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, "cuda")
         nb = c.n * 6 * 8
         e2e = {"value": atom_steps_rank * ws / dt, "unit": "atom-steps/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 3 * 416}
@@ -399,6 +480,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.workload == "served":
+        run_served(args, wl)
     else:
         run_pta(args, wl)
 
