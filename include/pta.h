@@ -61,7 +61,8 @@ typedef enum {
     PTA_ENAN = -5,            /* a non-finite energy appeared during a burst           */
     PTA_ESTATE = -6,          /* the call is not valid in the context's state          */
     PTA_ERANGE = -7,          /* a coordinate left the range the mixed-precision
-                                 representation holds (|x| < 512 A)                    */
+                                 representation holds (|x| < 512 A), or a specimen
+                                 has more than 2^23 atoms                             */
     PTA_EUNSUPPORTED = -8,    /* an option this build does not provide                 */
     PTA_ECAPACITY = -9        /* the input exceeds the fixed scratch size of
                                  pta_neighbours_noalloc                              */
@@ -114,6 +115,9 @@ typedef struct {
     int neigh_cap;      /* neighbour-list capacity per atom, 0 = automatic     */
     int lanes;          /* threads per atom in the pair kernels: 0 = automatic,
                            else 1, 2, 4, 8 or 16                               */
+    int atoms_per_thread; /* atoms sharing one neighbour list and thread group in
+                           the mixed-precision kernels: 0 = automatic, 1 or 2
+                           (2 needs lanes 1 or 2; FP64 uses 1)                 */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each

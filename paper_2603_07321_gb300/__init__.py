@@ -68,7 +68,7 @@ class Params(ctypes.Structure):
                 ("tol_j", ctypes.c_double * 3), ("floor", ctypes.c_double * 3),
                 ("burst_steps", ctypes.c_int64), ("block_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("neigh_cap", ctypes.c_int),
-                ("lanes", ctypes.c_int)]
+                ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int)]
 
 
 class Averages(ctypes.Structure):

@@ -22,7 +22,8 @@ LIB = os.path.join(OUT, "libpta.so")
 SOURCES = ["pta_api.cu", "k_setup.cu", "k_neigh.cu", "k_pair_f32.cu", "k_pair_f64.cu",
            "k_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INC,
+         "-I" + CSRC]
 
 
 def _nvcc():

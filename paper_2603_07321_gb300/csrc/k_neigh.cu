@@ -56,7 +56,7 @@ __global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__
     int ci[3];
     for (int d = 0; d < 3; ++d)
         ci[d] = clampi((int)floor((x[d] - S.org[d]) * S.inv_h), 0, S.nc[d] - 1);
-    const int c = ci[0] + S.nc[0] * (ci[1] + S.nc[1] * ci[2]);
+    const int c = cell_rank(S.nc, ci[0], ci[1], ci[2]);
     S.atom_cell[a] = c;
     atomicAdd(&S.cell_cnt[c], 1);
 }
@@ -70,6 +70,47 @@ __global__ void k_scan(const SpecDev *__restrict__ specs, int force) {
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
+    if (S.G == 2) {
+        // units per cell, (count + 1) / 2, scanned into unit_cell
+        __shared__ int ucarry;
+        if (threadIdx.x == 0) ucarry = 0;
+        __syncthreads();
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
+            const int c = base + threadIdx.x;
+            const int v = (c < S.ncell) ? (S.cell_cnt[c] + 1) / 2 : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            if (w == 0) {
+                int t = wsum[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                wsum[lane] = t;
+            }
+            __syncthreads();
+            const int excl = ucarry + (w ? wsum[w - 1] : 0) + x - v;
+            if (c < S.ncell) S.unit_cell[c] = excl;
+            __syncthreads();
+            if (threadIdx.x == SCAN_THREADS - 1) ucarry = excl + v;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            S.unit_cell[S.ncell] = ucarry;
+            S.ctl->nunits = ucarry;
+        }
+        __syncthreads();
+    } else if (threadIdx.x == 0) {
+        S.ctl->nunits = S.n;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
         const int c = base + threadIdx.x;
@@ -183,88 +224,113 @@ __global__ void k_permute_scatter(const SpecDev *__restrict__ specs, const int *
     S.atom_cell[p] = ((const int *)(t + Lo.cell))[p];
 }
 
-// one thread per atom: scan the 27 cells around the atom's cell
+// G = 2: pair up the atoms of every cell (slots 2k, 2k+1 of the cell form a
+// unit; an odd cell ends with a one-atom unit), so a unit never spans cells
+__global__ void k_unit_table(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                             int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (S.G != 2 || !build_active(S, force)) return;
+    const int p = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (p >= S.n) return;
+    const int c = S.atom_cell[p];
+    const int r = p - S.cell_start[c];
+    if (r & 1) return;
+    const int cnt = S.cell_start[c + 1] - S.cell_start[c];
+    S.unit_first[S.unit_cell[c] + r / 2] = p | ((r + 1 < cnt) ? UNIT_SECOND : 0);
+}
+
+// exact list predicate between atoms a and j (FP32 first; the FP64 test
+// decides only the thin band around the list radius)
+__device__ __forceinline__ bool in_list(const SpecDev &S, int par, bool mixed, int a, double xa,
+                                        double ya, double za, float4 ha, float4 la, int j) {
+    if (mixed) {
+        const float4 hj = ((const float4 *)S.pos[par])[j];
+        const float4 lj = S.lo[par][j];
+        const float fx = (hj.x - ha.x) + (lj.x - la.x);
+        const float fy = (hj.y - ha.y) + (lj.y - la.y);
+        const float fz = (hj.z - ha.z) + (lj.z - la.z);
+        const float r2f = fx * fx + fy * fy + fz * fz;
+        if (r2f < S.f_rl2_lo) return true;
+        if (r2f >= S.f_rl2_hi) return false;
+        const double ddx = ((double)hj.x + (double)lj.x) - xa;
+        const double ddy = ((double)hj.y + (double)lj.y) - ya;
+        const double ddz = ((double)hj.z + (double)lj.z) - za;
+        const double r2 =
+            __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        return r2 < S.rl2;
+    }
+    const double4_32a q = ((const double4_32a *)S.pos[par])[j];
+    const double ddx = q.x - xa, ddy = q.y - ya, ddz = q.z - za;
+    const double r2 =
+        __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+    return r2 < S.rl2;
+}
+
+// one thread per unit of G consecutive atoms: the unit's list is the union of
+// its atoms' lists (every j within the list radius of at least one atom of
+// the unit other than j itself), gathered from the box of cells around the
+// unit's cells in (z, y, x) order, each cell's atoms in slot order
 __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs,
                                                const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     if (!build_active(S, force)) return;
-    const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    const int u = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
     const int par = S.ctl->parity;
     int cnt = 0;
-    if (a < S.n) {
-        double xa, ya, za;
-        load_pos64(S, par, a, xa, ya, za);
-        const int c = S.atom_cell[a];
-        const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
-        const long long base = nl_base(a, S.L, S.cap);
-        const int L = S.L;
+    if (u < S.ctl->nunits) {
         const bool mixed = S.prec != PTA_PREC_FP64;
-        float4 ha = make_float4(0, 0, 0, 0), la = ha;
-        if (mixed) {
-            ha = ((const float4 *)S.pos[par])[a];
-            la = S.lo[par][a];
+        int a0, ga;
+        unit_atoms(S, u, a0, ga);
+        double x[2], y[2], z[2];
+        float4 ha[2], la[2];
+        int cx[2], cy[2], cz[2];
+        for (int g = 0; g < ga; ++g) {
+            load_pos64(S, par, a0 + g, x[g], y[g], z[g]);
+            ha[g] = la[g] = make_float4(0, 0, 0, 0);
+            if (mixed) {
+                ha[g] = ((const float4 *)S.pos[par])[a0 + g];
+                la[g] = S.lo[par][a0 + g];
+            }
+            cell_coords(S.nc, S.atom_cell[a0 + g], cx[g], cy[g], cz[g]);
         }
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = cz + dz;
-            if (z < 0 || z >= S.nc[2]) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = cy + dy;
-                if (y < 0 || y >= S.nc[1]) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int x = cx + dx;
-                    if (x < 0 || x >= S.nc[0]) continue;
-                    const int cc = x + S.nc[0] * (y + S.nc[1] * z);
+        int lo[3] = {cx[0], cy[0], cz[0]}, hi[3] = {cx[0], cy[0], cz[0]};
+        for (int g = 1; g < ga; ++g) {
+            lo[0] = min(lo[0], cx[g]);
+            hi[0] = max(hi[0], cx[g]);
+            lo[1] = min(lo[1], cy[g]);
+            hi[1] = max(hi[1], cy[g]);
+            lo[2] = min(lo[2], cz[g]);
+            hi[2] = max(hi[2], cz[g]);
+        }
+        const long long base = nl_base(u, S.L, S.cap);
+        const int L = S.L;
+        for (int zz = max(lo[2] - 1, 0); zz <= min(hi[2] + 1, S.nc[2] - 1); ++zz)
+            for (int yy = max(lo[1] - 1, 0); yy <= min(hi[1] + 1, S.nc[1] - 1); ++yy)
+                for (int xx = max(lo[0] - 1, 0); xx <= min(hi[0] + 1, S.nc[0] - 1); ++xx) {
+                    const int cc = cell_rank(S.nc, xx, yy, zz);
                     const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
+                    const int code = nl_code(xx - cx[0], yy - cy[0], zz - cz[0]) << NL_JBITS;
                     for (int j = s; j < e; ++j) {
-                        if (j == a) continue;
-                        bool in;
-                        if (mixed) {
-                            // FP32 distance first; only the thin band around the list
-                            // radius is decided by the exact FP64 test
-                            const float4 hj = ((const float4 *)S.pos[par])[j];
-                            const float4 lj = S.lo[par][j];
-                            const float fx = (hj.x - ha.x) + (lj.x - la.x);
-                            const float fy = (hj.y - ha.y) + (lj.y - la.y);
-                            const float fz = (hj.z - ha.z) + (lj.z - la.z);
-                            const float r2f = fx * fx + fy * fy + fz * fz;
-                            if (r2f < S.f_rl2_lo) {
-                                in = true;
-                            } else if (r2f >= S.f_rl2_hi) {
-                                in = false;
-                            } else {
-                                const double ddx = ((double)hj.x + (double)lj.x) - xa;
-                                const double ddy = ((double)hj.y + (double)lj.y) - ya;
-                                const double ddz = ((double)hj.z + (double)lj.z) - za;
-                                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx),
-                                                                      __dmul_rn(ddy, ddy)),
-                                                            __dmul_rn(ddz, ddz));
-                                in = r2 < S.rl2;
-                            }
-                        } else {
-                            const double4_32a q = ((const double4_32a *)S.pos[par])[j];
-                            const double ddx = q.x - xa, ddy = q.y - ya, ddz = q.z - za;
-                            const double r2 = __dadd_rn(
-                                __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
-                                __dmul_rn(ddz, ddz));
-                            in = r2 < S.rl2;
-                        }
+                        bool in = false;
+                        for (int g = 0; g < ga && !in; ++g)
+                            in = (j != a0 + g) && in_list(S, par, mixed, a0 + g, x[g], y[g], z[g],
+                                                          ha[g], la[g], j);
                         if (in) {
-                            if (cnt < S.cap)
-                                S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
-                                    j | (((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << NL_JBITS);
+                            if (cnt < S.cap) S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] = j | code;
                             ++cnt;
                         }
                     }
                 }
+        S.nn[u] = cnt < S.cap ? cnt : S.cap;
+        for (int g = 0; g < ga; ++g) {
+            const int a = a0 + g;
+            S.ref[a] = make_float4((float)x[g], (float)y[g], (float)z[g], 0.f);
+            if (mixed) {
+                // the neighbour-visible record relative to the (new) cell centre
+                const float3 C = cell_centre(S, S.atom_cell[a]);
+                S.rel[par][a] = make_float4((ha[g].x - C.x) + la[g].x, (ha[g].y - C.y) + la[g].y,
+                                            (ha[g].z - C.z) + la[g].z, 0.f);
             }
-        }
-        S.nn[a] = cnt < S.cap ? cnt : S.cap;
-        S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
-        if (mixed) {
-            // the neighbour-visible record relative to the (new) cell centre
-            const float3 C = cell_centre(S, c);
-            S.rel[par][a] = make_float4((ha.x - C.x) + la.x, (ha.y - C.y) + la.y,
-                                        (ha.z - C.z) + la.z, 0.f);
         }
     }
     // block maximum of the counts, one atomic per block
@@ -296,6 +362,20 @@ __global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
     if (threadIdx.x == 0) S.ctl->max_nn = 0;
 }
 
+// one block: does any specimen of the table need a list build before its
+// next pair pass?  Sets the condition of the graph node that holds the build.
+__global__ void k_decide_rebuild(const SpecDev *__restrict__ specs, int nspec,
+                                 cudaGraphConditionalHandle handle) {
+    int need = 0;
+    for (int s = threadIdx.x; s < nspec; s += blockDim.x) need |= build_active(specs[s], 0);
+    need = __syncthreads_or(need);
+    if (threadIdx.x == 0) cudaGraphSetConditional(handle, need ? 1u : 0u);
+}
+
+void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_decide_rebuild<<<1, 128, 0, st>>>(t.specs, t.nspec, h);
+}
+
 void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_reset_maxnn<<<t.nspec, 32, 0, st>>>(t.specs, force);
     k_bin<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
@@ -304,6 +384,7 @@ void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_cell_sort<<<t.nblk_cell, CELL_WARPS * 32, 0, st>>>(t.specs, t.b2s_cell, force);
     k_permute_gather<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_permute_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_unit_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);
 }

@@ -48,173 +48,230 @@ struct PowF {
     }
 };
 
-template <int L, bool SC76>
+// The unit of work is one atom (G = 1) or two atoms of one cell (G = 2)
+// sharing one neighbour list (the union of their lists), handled by L lanes.
+// For every entry the displacement from the unit's first atom is formed
+// once; the second follows as d_1 = d_0 - (rel_1 - rel_0), which is exactly 0
+// for the entry that is the second atom itself (then skipped).
+
+template <int L, int G, bool SC76>
 __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restrict__ specs,
-                                                     const int *__restrict__ b2s, int force) {
+                                                        const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     const SpecCtl *ctl = S.ctl;
     if (!force && ctl->phase == PH_IDLE) return;
     const int par = ctl->parity;
-    constexpr int APB = TPB / L;
-    const int a = (blockIdx.x - S.blk_pair0) * APB + threadIdx.x / L;
+    constexpr int UPB = TPB / L;
+    const int u = (blockIdx.x - S.blk_pair0) * UPB + threadIdx.x / L;
     const int l = threadIdx.x % L;
-    const bool valid = a < S.n;
+    const bool valid = u < ctl->nunits;
     const float4 *__restrict__ rel = S.rel[par];
     const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, Am = S.pot.f_Am, Bm = S.pot.f_Bm,
                 rc = S.pot.f_rc, h = S.f_h;
     const int m = S.pot.m;
-    float rho = 0.f;
-    float4 ra = make_float4(0, 0, 0, 0);
+    int a0 = 0, ga = 0;
+    if (valid) unit_atoms(S, u, a0, ga);
+    float rho[G];
+    float4 ra[G];
+    float3 dg[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        rho[g] = 0.f;
+        ra[g] = make_float4(0, 0, 0, 0);
+        dg[g] = make_float3(0, 0, 0);
+    }
     if (valid) {
-        ra = rel[a];
-        const int nn = S.nn[a];
-        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (g < ga) ra[g] = rel[a0 + g];
+        if (G > 1 && ga > 1) {
+            // both atoms of a unit share a cell: the offset is rel_1 - rel_0
+            dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+        }
+        const int nn = S.nn[u];
+        const int *__restrict__ lst = S.nlist + nl_base(u, L, S.cap);
         // software pipeline: entry two iterations ahead, record one ahead
-        // (a slot past the end reads the atom itself, always in bounds)
-        int q = 0;  // iteration: neighbour k = q * L + l
-        int e1 = (l < nn) ? __ldg(lst + l) : a;
-        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a;
+        // (a slot past the end reads the unit's first atom, always in bounds)
+        int q = 0;  // iteration: entry k = q * L + l
+        int e1 = (l < nn) ? __ldg(lst + l) : a0;
+        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a0;
         float4 rn = __ldg(rel + (e1 & NL_JMASK));
         for (int k = l; k < nn; k += L, ++q) {
             const float4 rj = rn;
             const unsigned code = (unsigned)e1 >> NL_JBITS;
-            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a;
+            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a0;
             rn = __ldg(rel + (e2 & NL_JMASK));
             e1 = e2;
             e2 = e3;
-            const float dx = fmaf(nl_off(code), h, rj.x - ra.x);
-            const float dy = fmaf(nl_off(code >> 2), h, rj.y - ra.y);
-            const float dz = fmaf(nl_off(code >> 4), h, rj.z - ra.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < rc2) {
-                const float ir = rsqrtf(r2);
-                const float r = r2 * ir;
-                const float s = pa * ir;
-                rho += PowF<SC76>::pm(s, m) - Am + Bm * (r - rc);
+            const float dx = fmaf(nl_off(code), h, rj.x - ra[0].x);
+            const float dy = fmaf(nl_off(code >> 3), h, rj.y - ra[0].y);
+            const float dz = fmaf(nl_off(code >> 6), h, rj.z - ra[0].z);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float ex = dx - dg[g].x, ey = dy - dg[g].y, ez = dz - dg[g].z;
+                const float r2 = ex * ex + ey * ey + ez * ez;
+                if (r2 < rc2 && r2 > 0.f && g < ga) {
+                    const float ir = rsqrtf(r2);
+                    const float r = r2 * ir;
+                    const float s = pa * ir;
+                    rho[g] += PowF<SC76>::pm(s, m) - Am + Bm * (r - rc);
+                }
             }
         }
     }
-    rho = lane_sum<L>(rho);
+#pragma unroll
+    for (int g = 0; g < G; ++g) rho[g] = lane_sum<L>(rho[g]);
     if (valid && l == 0) {
-        const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
-        ((float4 *)S.posfp)[a] = make_float4(ra.x, ra.y, ra.z, fp);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= ga) continue;
+            const float fp = rho[g] > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho[g]) : 0.f;
+            ((float4 *)S.posfp)[a0 + g] = make_float4(ra[g].x, ra[g].y, ra[g].z, fp);
+        }
     }
 }
 
-template <int L, bool SC76>
+template <int L, int G, bool SC76>
 __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict__ specs,
-                                                   const int *__restrict__ b2s, int mode) {
+                                                      const int *__restrict__ b2s, int mode) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     SpecCtl *ctl = S.ctl;
     const int phase = ctl->phase;
     if (mode == MODE_STEP && phase == PH_IDLE) return;
     const int par = ctl->parity;
     const long long done = ctl->done, nsteps = ctl->nsteps;
-    constexpr int APB = TPB / L;
+    constexpr int UPB = TPB / L;
     const int lb = blockIdx.x - S.blk_pair0;
-    const int a = lb * APB + threadIdx.x / L;
+    const int u = lb * UPB + threadIdx.x / L;
     const int l = threadIdx.x % L;
-    const bool valid = a < S.n;
+    const bool valid = u < ctl->nunits;
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
     const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, rc = S.pot.f_rc, h = S.f_h;
     const float An = S.pot.f_An, Bn = S.pot.f_Bn, Bm = S.pot.f_Bm, eps = S.pot.f_eps;
     const int n = S.pot.n, m = S.pot.m;
     const float fn = (float)n, fm = (float)m;
-    float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f;
-    float4 lfa = make_float4(0, 0, 0, 0);
+    int a0 = 0, ga = 0;
+    if (valid) unit_atoms(S, u, a0, ga);
+    float fx[G], fy[G], fz[G], en[G];
+    float4 ra[G];
+    float3 dg[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        fx[g] = fy[g] = fz[g] = en[g] = 0.f;
+        ra[g] = make_float4(0, 0, 0, 0);
+        dg[g] = make_float3(0, 0, 0);
+    }
     if (valid) {
-        lfa = lf[a];
-        const int nn = S.nn[a];
-        const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (g < ga) ra[g] = lf[a0 + g];
+        if (G > 1 && ga > 1) {
+            dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+        }
+        const int nn = S.nn[u];
+        const int *__restrict__ lst = S.nlist + nl_base(u, L, S.cap);
         int q = 0;
-        int e1 = (l < nn) ? __ldg(lst + l) : a;
-        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a;
+        int e1 = (l < nn) ? __ldg(lst + l) : a0;
+        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a0;
         float4 rn = __ldg(lf + (e1 & NL_JMASK));
         for (int k = l; k < nn; k += L, ++q) {
             const float4 lj = rn;
             const unsigned code = (unsigned)e1 >> NL_JBITS;
-            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a;
+            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a0;
             rn = __ldg(lf + (e2 & NL_JMASK));
             e1 = e2;
             e2 = e3;
-            const float dx = fmaf(nl_off(code), h, lj.x - lfa.x);
-            const float dy = fmaf(nl_off(code >> 2), h, lj.y - lfa.y);
-            const float dz = fmaf(nl_off(code >> 4), h, lj.z - lfa.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < rc2) {
-                const float ir = rsqrtf(r2);
-                const float r = r2 * ir;
-                const float s = pa * ir;
-                float sn, sm;
-                PowF<SC76>::pw(s, n, m, sn, sm);
-                const float dphn = -fn * sn * ir + Bn;
-                const float dphm = -fm * sm * ir + Bm;
-                const float g = (eps * dphn + (lfa.w + lj.w) * dphm) * ir;
-                fx += g * dx;
-                fy += g * dy;
-                fz += g * dz;
-                en += sn - An + Bn * (r - rc);
+            const float dx = fmaf(nl_off(code), h, lj.x - ra[0].x);
+            const float dy = fmaf(nl_off(code >> 3), h, lj.y - ra[0].y);
+            const float dz = fmaf(nl_off(code >> 6), h, lj.z - ra[0].z);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float ex = dx - dg[g].x, ey = dy - dg[g].y, ez = dz - dg[g].z;
+                const float r2 = ex * ex + ey * ey + ez * ez;
+                if (r2 < rc2 && r2 > 0.f && g < ga) {
+                    const float ir = rsqrtf(r2);
+                    const float r = r2 * ir;
+                    const float s = pa * ir;
+                    float sn, sm;
+                    PowF<SC76>::pw(s, n, m, sn, sm);
+                    const float dphn = -fn * sn * ir + Bn;
+                    const float dphm = -fm * sm * ir + Bm;
+                    const float gg = (eps * dphn + (ra[g].w + lj.w) * dphm) * ir;
+                    fx[g] += gg * ex;
+                    fy[g] += gg * ey;
+                    fz[g] += gg * ez;
+                    en[g] += sn - An + Bn * (r - rc);
+                }
             }
         }
     }
-    fx = lane_sum<L>(fx);
-    fy = lane_sum<L>(fy);
-    fz = lane_sum<L>(fz);
-    en = lane_sum<L>(en);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        fx[g] = lane_sum<L>(fx[g]);
+        fy[g] = lane_sum<L>(fy[g]);
+        fz[g] = lane_sum<L>(fz[g]);
+        en[g] = lane_sum<L>(en[g]);
+    }
     float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f;
     if (valid && l == 0) {
-        const float fpa = lfa.w;
-        pe = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
-        const uint8_t flag = S.flags[a];
-        if (flag == FLAG_RIGHT) rr = -(S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
-        float4 v = ((const float4 *)S.vel)[a];
-        if (mode == MODE_EVAL) {
-            ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
-            double4_32a *o = (double4_32a *)S.eval_out;
-            o[S.orig[a]] = make_double4_32a(fx, fy, fz, pe);
-        } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int a = a0 + g;
+            if (g >= ga) continue;
+            const float fpa = ra[g].w;
+            const float pe_a = 0.5f * eps * en[g] + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
+            pe += pe_a;
+            const uint8_t flag = S.flags[a];
+            if (flag == FLAG_RIGHT) rr -= (S.axis == 0 ? fx[g] : (S.axis == 1 ? fy[g] : fz[g]));
+            float4 v = ((const float4 *)S.vel)[a];
+            if (mode == MODE_EVAL) {
+                ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+                double4_32a *o = (double4_32a *)S.eval_out;
+                o[S.orig[a]] = make_double4_32a(fx[g], fy[g], fz[g], pe_a);
+                continue;
+            }
             const float kh = S.f_acc_half;
             if (phase == PH_RUN) {
                 if (flag == FLAG_MOBILE) {
-                    v.x += fx * kh;
-                    v.y += fy * kh;
-                    v.z += fz * kh;
+                    v.x += fx[g] * kh;
+                    v.y += fy[g] * kh;
+                    v.z += fz[g] * kh;
                 }
-                ke = S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+                ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
             const float4 hia = ((const float4 *)S.pos[par])[a];
             const float4 loa = S.lo[par][a];
-            float h[3] = {hia.x, hia.y, hia.z}, q[3] = {loa.x, loa.y, loa.z};
+            float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
             const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
             if (start && flag == FLAG_MOBILE) {
-                v.x += fx * kh;
-                v.y += fy * kh;
-                v.z += fz * kh;
+                v.x += fx[g] * kh;
+                v.y += fy[g] * kh;
+                v.z += fz[g] * kh;
                 const float dt = S.f_dt;
-                q[0] += v.x * dt;
-                q[1] += v.y * dt;
-                q[2] += v.z * dt;
+                qq[0] += v.x * dt;
+                qq[1] += v.y * dt;
+                qq[2] += v.z * dt;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     // move whole grid quanta from lo to hi (both steps exact)
-                    const float sh = rintf(q[d] * (float)HI_SCALE) * (float)HI_QUANTUM;
-                    h[d] = h[d] + sh;
-                    q[d] = q[d] - sh;
+                    const float sh = rintf(qq[d] * (float)HI_SCALE) * (float)HI_QUANTUM;
+                    hh[d] = hh[d] + sh;
+                    qq[d] = qq[d] - sh;
                 }
-                if (fabsf(h[0]) > (float)MIXED_RANGE || fabsf(h[1]) > (float)MIXED_RANGE ||
-                    fabsf(h[2]) > (float)MIXED_RANGE)
+                if (fabsf(hh[0]) > (float)MIXED_RANGE || fabsf(hh[1]) > (float)MIXED_RANGE ||
+                    fabsf(hh[2]) > (float)MIXED_RANGE)
                     atomicOr(&ctl->err, ERR_RANGE);
             }
-            ((float4 *)S.pos[par ^ 1])[a] = make_float4(h[0], h[1], h[2], 0.f);
-            S.lo[par ^ 1][a] = make_float4(q[0], q[1], q[2], 0.f);
+            ((float4 *)S.pos[par ^ 1])[a] = make_float4(hh[0], hh[1], hh[2], 0.f);
+            S.lo[par ^ 1][a] = make_float4(qq[0], qq[1], qq[2], 0.f);
             const float3 C = cell_centre(S, S.atom_cell[a]);
-            S.rel[par ^ 1][a] = make_float4((h[0] - C.x) + q[0], (h[1] - C.y) + q[1],
-                                            (h[2] - C.z) + q[2], 0.f);
+            S.rel[par ^ 1][a] = make_float4((hh[0] - C.x) + qq[0], (hh[1] - C.y) + qq[1],
+                                            (hh[2] - C.z) + qq[2], 0.f);
             ((float4 *)S.vel)[a] = v;
             const float4 rf = S.ref[a];
-            const float ex = (h[0] - rf.x) + q[0], ey = (h[1] - rf.y) + q[1],
-                        ez = (h[2] - rf.z) + q[2];
-            d2 = ex * ex + ey * ey + ez * ez;
+            const float ex = (hh[0] - rf.x) + qq[0], ey = (hh[1] - rf.y) + qq[1],
+                        ez = (hh[2] - rf.z) + qq[2];
+            d2 = fmaxf(d2, ex * ex + ey * ey + ez * ez);
         }
     }
     ke = warp_sum(ke);
@@ -230,26 +287,30 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
 void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st);
 void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st);
 
+#define PTA_LG_SWITCH(KER, ARG)                                                      \
+    if (g.G == 2) {                                                                  \
+        switch (g.L) {                                                               \
+            case 1: KER<1, 2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            default: KER<2, 2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+        }                                                                            \
+    } else {                                                                         \
+        switch (g.L) {                                                               \
+            case 1: KER<1, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            case 2: KER<2, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            case 4: KER<4, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            case 8: KER<8, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            default: KER<16, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+        }                                                                            \
+    }
+
 template <bool SC76>
 static void density_f32(const Tab &t, const Group &g, int force, cudaStream_t st) {
-    switch (g.L) {
-        case 1: k_density_f32<1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 2: k_density_f32<2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 4: k_density_f32<4, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 8: k_density_f32<8, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        default: k_density_f32<16, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-    }
+    PTA_LG_SWITCH(k_density_f32, force)
 }
 
 template <bool SC76>
 static void force_f32(const Tab &t, const Group &g, int mode, cudaStream_t st) {
-    switch (g.L) {
-        case 1: k_force_f32<1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 2: k_force_f32<2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 4: k_force_f32<4, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 8: k_force_f32<8, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        default: k_force_f32<16, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-    }
+    PTA_LG_SWITCH(k_force_f32, mode)
 }
 
 void launch_density(const Tab &t, int force, cudaStream_t st) {

@@ -79,7 +79,7 @@ struct pta_ctx {
 struct Runner {
     std::vector<pta_ctx *> m;
     cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
     Allocator alloc;
     std::vector<DevBuf> bufs;
     std::vector<SpecDev> hspecs;
@@ -245,15 +245,20 @@ static PotDev make_pot(const pta_potential &p) {
 // sizes
 // ---------------------------------------------------------------------------
 struct Sizes {
-    long long n;
-    int L, cap, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
+    long long n, nunits;
+    int L, G, cap, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
     double h, org[3];
     size_t list_words;
     long long series_cap;
 };
 
-static int auto_lanes(long long n) {
-    long long t = THREADS_TARGET / std::max<long long>(n, 1);
+// threads per atom chosen from the specimen alone (so that a specimen runs
+// the same arithmetic alone and in a batch): FP64 specimens spread over the
+// whole GPU; mixed-precision ones aim at ~64K threads and let batching fill
+// the device
+static int auto_lanes(long long n, int prec) {
+    const long long target = prec == PTA_PREC_FP64 ? THREADS_TARGET : 65536;
+    long long t = target / std::max<long long>(n, 1);
     int L = 1;
     while (L * 2 <= t && L < 16) L *= 2;
     return L;
@@ -264,16 +269,25 @@ static int valid_lanes(int L) { return L == 1 || L == 2 || L == 4 || L == 8 || L
 static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pta_params &par,
                          Sizes *z) {
     z->n = 4LL * s.n_cells[0] * s.n_cells[1] * s.n_cells[2];
-    z->L = par.lanes ? par.lanes : auto_lanes(z->n);
+    z->L = par.lanes ? par.lanes : auto_lanes(z->n, par.precision);
+    // atoms per thread group: 1 unless asked for 2 (two atoms of one cell
+    // sharing a union list read each neighbour record once for both, but the
+    // two per-atom branches per entry cost more issue slots than the saved
+    // reads on GB300, measured on the 470,596-atom cube)
+    z->G = par.atoms_per_thread ? par.atoms_per_thread : 1;
+    z->nunits = z->n;  // capacity; G = 2 sets the exact count at every build (below)
     const double rl = p.rc + par.skin;
     if (par.neigh_cap > 0) {
         z->cap = (int)round_up((size_t)par.neigh_cap, 32);
     } else {
+        // atoms of one unit lie within ~3 A of each other: the union list
+        // covers a sphere about 1.6 A wider
         const double dens = 4.0 / (s.a0 * s.a0 * s.a0);
-        const double nb = 4.0 / 3.0 * 3.141592653589793 * rl * rl * rl * dens;
+        const double rr = rl + (z->G > 1 ? 1.6 : 0.0);
+        const double nb = 4.0 / 3.0 * 3.141592653589793 * rr * rr * rr * dens;
         z->cap = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
     }
-    z->nblk_pair = (int)((z->n * z->L + TPB - 1) / TPB);
+    z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
     // cell edge a multiple of 2^-11 A and grid origin on the 2^-12 A grid, so
     // that cell centres and centre differences are exact in FP32
@@ -294,8 +308,11 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     if (ncell > (1LL << 30)) return PTA_EINVAL;
     z->ncell = (int)ncell;
     z->nblk_cell = (z->ncell + CELL_WARPS - 1) / CELL_WARPS;
-    const long long G = 32 / z->L;
-    z->list_words = (size_t)((z->n + G - 1) / G) * G * z->cap;
+    // G = 2: at most one one-atom unit per cell besides the pairs
+    if (z->G == 2) z->nunits = std::min<long long>(z->n, (z->n + 1) / 2 + z->ncell);
+    z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
+    const long long W = 32 / z->L;
+    z->list_words = (size_t)((z->nunits + W - 1) / W) * W * z->cap;
     z->series_cap = std::max<long long>(par.burst_steps, 1);
     return PTA_OK;
 }
@@ -325,7 +342,11 @@ static size_t footprint(const Sizes &z, int prec) {
     add(4 * n);                      // orig
     add(perm_layout(n, prec).total); // permutation scratch
     add(4 * z.list_words);           // nlist
-    add(4 * n);                      // nn
+    add(4 * (size_t)z.nunits);       // nn
+    if (z.G == 2) {
+        add(4 * n);                  // unit_first
+        add(4 * ((size_t)z.ncell + 1));  // unit_cell
+    }
     add(32 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
@@ -350,9 +371,13 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
     if (par->burst_steps < 1 || par->block_steps < 1) return PTA_EINVAL;
     if (par->precision != PTA_PREC_FP64 && par->precision != PTA_PREC_MIXED) return PTA_EINVAL;
     if (par->lanes != 0 && !valid_lanes(par->lanes)) return PTA_EINVAL;
+    if (par->atoms_per_thread < 0 || par->atoms_per_thread > 2) return PTA_EINVAL;
+    if (par->atoms_per_thread == 2 &&
+        (par->precision == PTA_PREC_FP64 || (par->lanes != 0 && par->lanes > 2)))
+        return PTA_EUNSUPPORTED;
     if (par->neigh_cap < 0 || par->neigh_cap > 4096) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
-    if (n > (1LL << 30)) return PTA_EINVAL;
+    if (n > (long long)MAX_ATOMS) return PTA_ERANGE;
     if (par->precision == PTA_PREC_MIXED) {
         for (int d = 0; d < 3; ++d)
             if (s->n_cells[d] * s->a0 * 1.5 > MIXED_RANGE) return PTA_ERANGE;
@@ -374,24 +399,82 @@ static void runner_free(Runner *r) {
     dev_release_all(r);
     if (r->h_pin) cudaFreeHost(r->h_pin);
     if (r->cap) cudaStreamDestroy(r->cap);
+    if (r->cap2) cudaStreamDestroy(r->cap2);
     delete r;
 }
 
+// Graph of `iters` fine-step iterations.  Each iteration is
+//   [decide] -> IF(a list build is needed) { build kernels } -> density -> force
+// where the decide kernel sets the IF node's condition on the device, so
+// the build kernels are skipped without a launch when no specimen needs
+// them.  With `timed`, event-record nodes bracket the parts of each
+// iteration (events cannot sit inside a conditional body, so the build
+// time is measured around the whole conditional).
 static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed = false) {
     cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < iters; ++i) {
+    CK(cudaGraphCreate(&g, 0));
+    std::vector<cudaGraphConditionalHandle> handles(iters);
+    for (int i = 0; i < iters; ++i)
+        if (cudaGraphConditionalHandleCreate(&handles[i], g, 0, cudaGraphCondAssignDefault) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return PTA_ECUDA;
+        }
+    cudaError_t e = cudaStreamBeginCaptureToGraph(r->cap, g, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    int rc = (e == cudaSuccess) ? PTA_OK : PTA_ECUDA;
+    for (int i = 0; i < iters && rc == PTA_OK; ++i) {
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
-        launch_rebuild(r->tab, 0, r->cap);
+        launch_decide_rebuild(r->tab, handles[i], r->cap);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edata = nullptr;
+        size_t ndeps = 0;
+        if (cudaStreamGetCaptureInfo(r->cap, &cs, nullptr, &cg, &deps, &edata, &ndeps) !=
+            cudaSuccess) {
+            rc = PTA_ECUDA;
+            break;
+        }
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handles[i];
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        if (cudaGraphAddNode(&cnode, cg, deps, edata, ndeps, &np) != cudaSuccess) {
+            rc = PTA_ECUDA;
+            break;
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if (cudaStreamUpdateCaptureDependencies(r->cap, &cnode, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies) != cudaSuccess) {
+            rc = PTA_ECUDA;
+            break;
+        }
+        if (cudaStreamBeginCaptureToGraph(r->cap2, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = PTA_ECUDA;
+            break;
+        }
+        launch_rebuild(r->tab, 0, r->cap2);
+        cudaGraph_t bout = nullptr;
+        if (cudaStreamEndCapture(r->cap2, &bout) != cudaSuccess) {
+            rc = PTA_ECUDA;
+            break;
+        }
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
         launch_density(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 2], r->cap, cudaEventRecordExternal);
         launch_force(r->tab, MODE_STEP, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 3], r->cap, cudaEventRecordExternal);
     }
-    cudaError_t e = cudaStreamEndCapture(r->cap, &g);
-    if (e != cudaSuccess) {
+    cudaGraph_t gout = nullptr;
+    e = cudaStreamEndCapture(r->cap, &gout);
+    if (e != cudaSuccess || rc != PTA_OK) {
         cudaGetLastError();
+        cudaGraphDestroy(g);
         return PTA_ECUDA;
     }
     e = cudaGraphInstantiate(out, g, 0);
@@ -410,7 +493,7 @@ static int runner_upload(Runner *r) {
     int blk_atom = 0, blk_cell = 0;
     std::vector<int> b2s_atom, b2s_cell;
     struct Key {
-        int prec, L, sc76;
+        int prec, L, G, sc76;
     };
     std::vector<Key> keys;
     std::vector<std::vector<int>> gb2s;
@@ -425,10 +508,12 @@ static int runner_upload(Runner *r) {
         for (int b = 0; b < s.nblk_cell; ++b) b2s_cell.push_back(i);
         int g = -1;
         for (size_t q = 0; q < keys.size(); ++q)
-            if (keys[q].prec == s.prec && keys[q].L == s.L && keys[q].sc76 == s.pot.sc76) g = (int)q;
+            if (keys[q].prec == s.prec && keys[q].L == s.L && keys[q].G == s.G &&
+                keys[q].sc76 == s.pot.sc76)
+                g = (int)q;
         if (g < 0) {
             if (keys.size() >= 8) return PTA_EUNSUPPORTED;
-            keys.push_back({s.prec, s.L, s.pot.sc76});
+            keys.push_back({s.prec, s.L, s.G, s.pot.sc76});
             gb2s.emplace_back();
             g = (int)keys.size() - 1;
         }
@@ -484,6 +569,7 @@ static int runner_upload(Runner *r) {
     for (size_t q = 0; q < keys.size(); ++q) {
         t.grp[q].prec = keys[q].prec;
         t.grp[q].L = keys[q].L;
+        t.grp[q].G = keys[q].G;
         t.grp[q].sc76 = keys[q].sc76;
         t.grp[q].b2s = tabs + off;
         t.grp[q].nblk = (int)gb2s[q].size();
@@ -513,7 +599,9 @@ static int runner_create(pta_ctx *const *members, int k, Runner **out) {
     r->stream = members[0]->stream;
     r->alloc = members[0]->alloc;
     int rc = PTA_OK;
-    if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) rc = PTA_ECUDA;
+    if (cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&r->cap2, cudaStreamNonBlocking) != cudaSuccess)
+        rc = PTA_ECUDA;
     if (rc == PTA_OK) rc = runner_upload(r);
     if (rc == PTA_OK) rc = capture_iters(r, CHUNK, &r->g_chunk);
     if (rc == PTA_OK) rc = capture_iters(r, 1, &r->g_one);
@@ -818,7 +906,11 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     AL(orig, 4 * n, int *);
     AL(perm_tmp, perm_layout(n, c->par.precision).total, void *);
     AL(nlist, 4 * z.list_words, int *);
-    AL(nn, 4 * n, int *);
+    AL(nn, 4 * (size_t)z.nunits, int *);
+    if (z.G == 2) {
+        AL(unit_first, 4 * n, int *);
+        AL(unit_cell, 4 * ((size_t)z.ncell + 1), int *);
+    }
     AL(part, 32 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
@@ -860,6 +952,8 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     std::memset(&s, 0, sizeof(s));
     s.n = (int)z.n;
     s.L = z.L;
+    s.G = z.G;
+    s.nunits = (int)z.nunits;
     s.prec = c->par.precision;
     s.axis = c->spec.load_axis;
     s.cap = z.cap;
@@ -1097,28 +1191,64 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     launch_rebuild(r->tab, 1, c->stream);
     CKR(launch_check());
     const SpecDev &s = c->hd;
-    std::vector<int> nn((size_t)n), raw;
+    std::vector<int> nn((size_t)s.nunits), raw;
     SpecCtl ctl;
-    CK(cudaMemcpyAsync(nn.data(), s.nn, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(nn.data(), s.nn, 4 * (size_t)s.nunits, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-    const long long G = 32 / s.L;
-    const size_t words = (size_t)((n + G - 1) / G) * G * s.cap;
+    const long long W = 32 / s.L;
+    const size_t words = (size_t)((s.nunits + W - 1) / W) * W * s.cap;
     raw.resize(words);
     std::vector<int> orig;
     CK(cudaMemcpyAsync(raw.data(), s.nlist, 4 * words, cudaMemcpyDeviceToHost, c->stream));
     CKR(fetch_orig(c, orig));
+    // exact positions in slot order, for splitting a unit's union list
+    std::vector<double> pos;
+    if (s.G > 1) {
+        launch_export(c->hd, c->d_self, c->stream);
+        CKR(launch_check());
+        pos.resize(3 * (size_t)n);
+        CK(cudaMemcpyAsync(pos.data(), s.stage, 24 * (size_t)n, cudaMemcpyDeviceToHost,
+                           c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     *max_count = ctl.max_nn;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
-    if (ctl.max_nn > cap) return PTA_EINVAL;
-    for (int64_t a = 0; a < n; ++a) {
-        const int64_t o = orig[a];
-        if (counts) counts[o] = nn[a];
-        if (list)
-            for (int k = 0; k < nn[a]; ++k)
-                list[o * (int64_t)cap + k] =
-                    orig[raw[(size_t)nl_index((int)a, k, s.L, s.cap)] & NL_JMASK];
+    std::vector<int> ufirst;
+    if (s.G == 2) {
+        ufirst.resize((size_t)ctl.nunits);
+        CK(cudaMemcpy(ufirst.data(), s.unit_first, 4 * (size_t)ctl.nunits, cudaMemcpyDeviceToHost));
     }
+    std::vector<int> row;
+    int maxc = 0;
+    for (int64_t u = 0; u < ctl.nunits; ++u) {
+        int a0 = (int)u, ga = 1;
+        if (s.G == 2) {
+            a0 = ufirst[u] & (UNIT_SECOND - 1);
+            ga = (ufirst[u] & UNIT_SECOND) ? 2 : 1;
+        }
+        for (int g = 0; g < ga; ++g) {
+            const int64_t a = a0 + g;
+            row.clear();
+            for (int k = 0; k < nn[u]; ++k) {
+                const int j = raw[(size_t)nl_index((int)u, k, s.L, s.cap)] & NL_JMASK;
+                if (s.G > 1) {
+                    // the same FP64 predicate as the list build (no contraction)
+                    if (j == a) continue;
+                    const double *pa = &pos[3 * (size_t)orig[a]], *pj = &pos[3 * (size_t)orig[j]];
+                    const double dx = pj[0] - pa[0], dy = pj[1] - pa[1], dz = pj[2] - pa[2];
+                    if (!((dx * dx + dy * dy) + dz * dz < s.rl2)) continue;
+                }
+                row.push_back(orig[j]);
+            }
+            maxc = std::max<int>(maxc, (int)row.size());
+            const int64_t o = orig[a];
+            if (counts) counts[o] = (int32_t)row.size();
+            if ((int)row.size() > cap) return PTA_EINVAL;
+            if (list)
+                for (size_t k = 0; k < row.size(); ++k) list[o * (int64_t)cap + k] = row[k];
+        }
+    }
+    *max_count = maxc;
     return PTA_OK;
 }
 

@@ -58,6 +58,7 @@ struct SpecCtl {
     int list_L;                // lanes the current list layout was built for
     int rebuilds;              // list builds in the current burst
     int max_nn;                // largest neighbour count at the last build
+    int nunits;                // units in use (G = 2: pairs of atoms of one cell)
     double sum[3];             // running sums of K, U, T over the burst
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
@@ -68,7 +69,9 @@ struct SpecCtl {
 struct SpecDev {
     // sizes
     int n, L, prec, axis, cap;
-    int blk_pair0, nblk_pair;  // pair kernels: TPB/L atoms per block
+    int G, nunits;             // atoms per unit (one thread group and one list per unit);
+                               // nunits is the capacity (units in use: SpecCtl::nunits)
+    int blk_pair0, nblk_pair;  // pair kernels: TPB/L units per block
     int blk_atom0, nblk_atom;  // one thread per atom
     int blk_cell0, nblk_cell;  // one warp per cell
     int spec_index;            // index of this specimen in the launch table
@@ -102,6 +105,8 @@ struct SpecDev {
     float4 *ref;    // positions at the last list build (skin test)
     int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
     int *orig;        // original index (creation order) of the atom stored at each slot
+    int *unit_first;  // G = 2: first slot of each unit | (1 << 30) when it has a second atom
+    int *unit_cell;   // G = 2: first unit of each cell (ncell + 1)
     void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
     int *nlist, *nn;
     double *part;       // per pair block: K, U, R, max displacement^2
@@ -113,7 +118,7 @@ struct SpecDev {
 };
 
 struct Group {
-    int prec, L, sc76;
+    int prec, L, G, sc76;
     const int *b2s;
     int nblk;
 };
@@ -130,22 +135,47 @@ struct Tab {
     Group grp[8];
 };
 
-// Verlet-list entry: neighbour index in the low 26 bits, the neighbour's
-// cell offset (dx, dy, dz) in {-1, 0, 1}^3 relative to the atom's cell in
-// the high 6 bits as (dx+1) | (dy+1) << 2 | (dz+1) << 4.  With cell centres
-// and the cell edge h on exact grids, r_j - r_i = (rel_j - rel_i) + h * d.
-constexpr int NL_JBITS = 26;
+// Verlet-list entry (one list per unit of G consecutive atoms): neighbour
+// index in the low 23 bits, the neighbour's cell offset (dx, dy, dz) relative
+// to the cell of the unit's first atom in the high 9 bits, 3 bits per axis
+// holding d + 3.  With cell centres and the cell edge h on exact grids,
+// r_j - r_i = (rel_j - rel_i) + h * d.
+constexpr int NL_JBITS = 23;
 constexpr int NL_JMASK = (1 << NL_JBITS) - 1;
+constexpr int MAX_ATOMS = 1 << NL_JBITS;
 
-// FP32 value (code & 3) - 1 in {-1, 0, 1}, without an integer conversion:
-// 0x4B400000 is 1.5 * 2^23, whose last mantissa bits take small integers exactly
-__device__ __forceinline__ float nl_off(unsigned bits) {
-    return __int_as_float(0x4B400000 | (int)(bits & 3u)) - 12582913.0f;
+__host__ __device__ __forceinline__ int nl_code(int dx, int dy, int dz) {
+    return (dx + 3) | ((dy + 3) << 3) | ((dz + 3) << 6);
 }
 
-// centre of cell c (exact in FP32: org on a 2^-12 grid, h a multiple of 2^-11)
-__device__ __forceinline__ float3 cell_centre(const SpecDev &S, int c) {
-    const int cx = c % S.nc[0], cy = (c / S.nc[0]) % S.nc[1], cz = c / (S.nc[0] * S.nc[1]);
+// FP32 value (bits & 7) - 3, without an integer conversion: 0x4B400000 is
+// 1.5 * 2^23, whose last mantissa bits take small integers exactly
+__device__ __forceinline__ float nl_off(unsigned bits) {
+    return __int_as_float(0x4B400000 | (int)(bits & 7u)) - 12582915.0f;
+}
+
+// Cells are numbered along a serpentine path (x reverses on every other row,
+// y on every other layer), so that consecutive cells are face neighbours and
+// consecutive atoms of the cell-sorted order lie in the same or adjacent cells.
+__host__ __device__ __forceinline__ int cell_rank(const int nc[3], int x, int y, int z) {
+    const int yr = (z & 1) ? nc[1] - 1 - y : y;
+    const int t = z * nc[1] + yr;
+    const int xr = (t & 1) ? nc[0] - 1 - x : x;
+    return t * nc[0] + xr;
+}
+__host__ __device__ __forceinline__ void cell_coords(const int nc[3], int r, int &x, int &y, int &z) {
+    const int t = r / nc[0], xr = r % nc[0];
+    z = t / nc[1];
+    const int yr = t % nc[1];
+    y = (z & 1) ? nc[1] - 1 - yr : yr;
+    x = (t & 1) ? nc[0] - 1 - xr : xr;
+}
+
+// centre of the cell of rank r (exact in FP32: org on a 2^-12 grid, h a
+// multiple of 2^-11)
+__device__ __forceinline__ float3 cell_centre(const SpecDev &S, int r) {
+    int cx, cy, cz;
+    cell_coords(S.nc, r, cx, cy, cz);
     return make_float3(S.f_org[0] + ((float)cx + 0.5f) * S.f_h,
                        S.f_org[1] + ((float)cy + 0.5f) * S.f_h,
                        S.f_org[2] + ((float)cz + 0.5f) * S.f_h);
@@ -176,6 +206,19 @@ __host__ __device__ inline PermLayout perm_layout(size_t n, int prec) {
     return L;
 }
 
+// atoms of unit u: first slot and count (G = 1: the unit is the atom)
+constexpr int UNIT_SECOND = 1 << 30;
+__device__ __forceinline__ void unit_atoms(const SpecDev &S, int u, int &a0, int &ga) {
+    if (S.G == 1) {
+        a0 = u;
+        ga = 1;
+    } else {
+        const int info = S.unit_first[u];
+        a0 = info & (UNIT_SECOND - 1);
+        ga = (info & UNIT_SECOND) ? 2 : 1;
+    }
+}
+
 // neighbour-list word of neighbour k of atom a for L lanes per atom: atoms
 // are grouped 32/L per warp; for each iteration q = k / L the warp's 32
 // words are contiguous, lane (a % (32/L)) * L + k % L.
@@ -202,6 +245,7 @@ void launch_burst_end(const Tab &t, int slot, pta_averages *out, cudaStream_t st
 void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
 void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
 void launch_rebuild(const Tab &t, int force, cudaStream_t st);
+void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_density(const Tab &t, int force, cudaStream_t st);
 void launch_force(const Tab &t, int mode, cudaStream_t st);
 

@@ -30,11 +30,11 @@ def test_create_matches_oracle(P, oracle, prec, shape, axis):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lanes", [1, 4, 16])
+@pytest.mark.parametrize("prec,lanes,apt", [(0, 1, 1), (0, 4, 1), (0, 16, 1), (1, 1, 1),
+                                             (1, 4, 1), (1, 16, 1), (1, 1, 2), (1, 2, 2)])
 @pytest.mark.parametrize("shape", [(5, 4, 6), (7, 7, 7)])
-def test_neighbour_sets_bit_exact(P, oracle, prec, lanes, shape):
-    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=prec, lanes=lanes)
+def test_neighbour_sets_bit_exact(P, oracle, prec, lanes, apt, shape):
+    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=prec, lanes=lanes, atoms_per_thread=apt)
     pos = on_grid(PI.jittered_fcc(shape, 0.35, seed=sum(shape) + lanes))
     ctx.set_state(pos, np.zeros_like(pos))
     c_gpu, l_gpu = ctx.neighbours(cap=512)
@@ -64,10 +64,10 @@ def ctx_pot(oracle, ctx):
     return oracle.Potential(eps=p.eps, c=p.c, a=p.a, rc=p.rc, n=p.n, m=p.m)
 
 
-@pytest.mark.parametrize("lanes", [1, 4, 16])
-def test_forces_mixed(P, oracle, lanes):
+@pytest.mark.parametrize("lanes,apt", [(1, 1), (4, 1), (16, 1), (1, 2), (2, 2)])
+def test_forces_mixed(P, oracle, lanes, apt):
     shape = (6, 5, 7)
-    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes)
+    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes, atoms_per_thread=apt)
     pos = on_grid(PI.gaussian_jitter_fcc(shape, 0.1, seed=10 + lanes))
     ctx.set_state(pos, np.zeros_like(pos))
     f, pe, _ = ctx.forces()
@@ -251,11 +251,27 @@ def test_neighbour_overflow_is_reported(P, oracle):
     ctx.close()
 
 
+def test_two_atoms_per_thread_trajectory_matches_one(P, oracle):
+    # same arithmetic per pair up to FP32 rounding: 100-step trajectories agree closely
+    out = []
+    for apt in (1, 2):
+        ctx = P.Ctx((7, 6, 8), T0=300.0, seed=8, precision=P.PREC_MIXED, lanes=1,
+                    atoms_per_thread=apt)
+        ctx.apply_strain(1e-3)
+        ctx.fine_burst(100)
+        out.append((ctx.series().copy(), ctx.get_state()[0]))
+        ctx.close()
+    assert np.allclose(out[0][0][:, :2], out[1][0][:, :2], rtol=1e-5)
+    assert np.max(np.abs(out[0][1] - out[1][1])) < 1e-3
+
+
 def test_invalid_arguments(P):
     with pytest.raises(P.PTAError):
         P.Ctx((2, 2, 2))  # fewer than 3 cells along the load axis
     with pytest.raises(P.PTAError):
         P.Ctx((4, 4, 4), lanes=3)
+    with pytest.raises(P.PTAError):
+        P.Ctx((4, 4, 4), precision=P.PREC_FP64, atoms_per_thread=2)
     ctx = P.Ctx((4, 4, 4))
     with pytest.raises(P.PTAError):
         ctx.fine_burst(0)
