@@ -309,19 +309,21 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                 for (int xx = max(lo[0] - 1, 0); xx <= min(hi[0] + 1, S.nc[0] - 1); ++xx) {
                     const int cc = cell_rank(S.nc, xx, yy, zz);
                     const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
-                    const int code = nl_code(xx - cx[0], yy - cy[0], zz - cz[0]) << NL_JBITS;
+                    const unsigned code = nl_entry(0, xx - cx[0], yy - cy[0], zz - cz[0]);
                     for (int j = s; j < e; ++j) {
                         bool in = false;
                         for (int g = 0; g < ga && !in; ++g)
                             in = (j != a0 + g) && in_list(S, par, mixed, a0 + g, x[g], y[g], z[g],
                                                           ha[g], la[g], j);
                         if (in) {
-                            if (cnt < S.cap) S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] = j | code;
+                            if (cnt < S.cap_use)
+                                S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
+                                    (int)(((unsigned)j << NL_CODE_BITS) | code);
                             ++cnt;
                         }
                     }
                 }
-        S.nn[u] = cnt < S.cap ? cnt : S.cap;
+        S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
         for (int g = 0; g < ga; ++g) {
             const int a = a0 + g;
             S.ref[a] = make_float4((float)x[g], (float)y[g], (float)z[g], 0.f);
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         for (int w = 1; w < TPB / 32; ++w) m = max(m, smax[w]);
         m = max(m, smax[0]);
         atomicMax(&S.ctl->max_nn, m);
-        if (m > S.cap) atomicOr(&S.ctl->err, ERR_OVERFLOW);
+        if (m > S.cap_use) atomicOr(&S.ctl->err, ERR_OVERFLOW);
     }
 }
 

@@ -53,6 +53,64 @@ struct PowF {
 // For every entry the displacement from the unit's first atom is formed
 // once; the second follows as d_1 = d_0 - (rel_1 - rel_0), which is exactly 0
 // for the entry that is the second atom itself (then skipped).
+//
+// The entry loop is unrolled by two; the next two entries are read before
+// the current two are evaluated.  Those reads go past a unit's count into
+// the four spare iterations every list keeps, whose entries are valid
+// indices, so the loop carries no bounds tests.
+
+// displacement of entry e's atom (record x) from the unit's first atom (record r0)
+__device__ __forceinline__ float3 entry_disp(unsigned e, float4 x, float4 r0, float h, float h8,
+                                             float h64) {
+    return make_float3(fmaf(nl_offx(e), h, x.x - r0.x), fmaf(nl_offy(e), h8, x.y - r0.y),
+                       fmaf(nl_offz(e), h64, x.z - r0.z));
+}
+
+template <int G, bool SC76>
+struct DensityAcc {
+    float rho[G];
+    __device__ __forceinline__ void add(const SpecDev &S, float3 d, const float3 *dg, int ga) {
+        const float rc2 = S.pot.f_rc2;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ex = d.x - dg[g].x, ey = d.y - dg[g].y, ez = d.z - dg[g].z;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (r2 < rc2 && (G == 1 || (r2 > 0.f && g < ga))) {
+                const float ir = rsqrtf(r2);
+                const float s = S.pot.f_a * ir;
+                rho[g] += PowF<SC76>::pm(s, S.pot.m) - S.pot.f_Am + S.pot.f_Bm * (r2 * ir - S.pot.f_rc);
+            }
+        }
+    }
+};
+
+template <int G, bool SC76>
+struct ForceAcc {
+    float fx[G], fy[G], fz[G], en[G];
+    __device__ __forceinline__ void add(const SpecDev &S, float3 d, float fpj, const float3 *dg,
+                                        const float4 *ra, int ga) {
+        const float rc2 = S.pot.f_rc2;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ex = d.x - dg[g].x, ey = d.y - dg[g].y, ez = d.z - dg[g].z;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (r2 < rc2 && (G == 1 || (r2 > 0.f && g < ga))) {
+                const float ir = rsqrtf(r2);
+                const float r = r2 * ir;
+                const float s = S.pot.f_a * ir;
+                float sn, sm;
+                PowF<SC76>::pw(s, S.pot.n, S.pot.m, sn, sm);
+                const float dphn = -(float)S.pot.n * sn * ir + S.pot.f_Bn;
+                const float dphm = -(float)S.pot.m * sm * ir + S.pot.f_Bm;
+                const float gg = (S.pot.f_eps * dphn + (ra[g].w + fpj) * dphm) * ir;
+                fx[g] += gg * ex;
+                fy[g] += gg * ey;
+                fz[g] += gg * ez;
+                en[g] += sn - S.pot.f_An + S.pot.f_Bn * (r - S.pot.f_rc);
+            }
+        }
+    }
+};
 
 template <int L, int G, bool SC76>
 __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restrict__ specs,
@@ -66,17 +124,15 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
     const int l = threadIdx.x % L;
     const bool valid = u < ctl->nunits;
     const float4 *__restrict__ rel = S.rel[par];
-    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, Am = S.pot.f_Am, Bm = S.pot.f_Bm,
-                rc = S.pot.f_rc, h = S.f_h;
-    const int m = S.pot.m;
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
     int a0 = 0, ga = 0;
     if (valid) unit_atoms(S, u, a0, ga);
-    float rho[G];
+    DensityAcc<G, SC76> acc;
     float4 ra[G];
     float3 dg[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        rho[g] = 0.f;
+        acc.rho[g] = 0.f;
         ra[g] = make_float4(0, 0, 0, 0);
         dg[g] = make_float3(0, 0, 0);
     }
@@ -84,48 +140,30 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (g < ga) ra[g] = rel[a0 + g];
-        if (G > 1 && ga > 1) {
-            // both atoms of a unit share a cell: the offset is rel_1 - rel_0
+        if (G > 1 && ga > 1)  // both atoms share a cell: the offset is rel_1 - rel_0
             dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
-        }
         const int nn = S.nn[u];
-        const int *__restrict__ lst = S.nlist + nl_base(u, L, S.cap);
-        // software pipeline: entry two iterations ahead, record one ahead
-        // (a slot past the end reads the unit's first atom, always in bounds)
-        int q = 0;  // iteration: entry k = q * L + l
-        int e1 = (l < nn) ? __ldg(lst + l) : a0;
-        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a0;
-        float4 rn = __ldg(rel + (e1 & NL_JMASK));
-        for (int k = l; k < nn; k += L, ++q) {
-            const float4 rj = rn;
-            const unsigned code = (unsigned)e1 >> NL_JBITS;
-            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a0;
-            rn = __ldg(rel + (e2 & NL_JMASK));
-            e1 = e2;
-            e2 = e3;
-            const float dx = fmaf(nl_off(code), h, rj.x - ra[0].x);
-            const float dy = fmaf(nl_off(code >> 3), h, rj.y - ra[0].y);
-            const float dz = fmaf(nl_off(code >> 6), h, rj.z - ra[0].z);
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float ex = dx - dg[g].x, ey = dy - dg[g].y, ez = dz - dg[g].z;
-                const float r2 = ex * ex + ey * ey + ez * ez;
-                if (r2 < rc2 && r2 > 0.f && g < ga) {
-                    const float ir = rsqrtf(r2);
-                    const float r = r2 * ir;
-                    const float s = pa * ir;
-                    rho[g] += PowF<SC76>::pm(s, m) - Am + Bm * (r - rc);
-                }
-            }
+        const unsigned *__restrict__ lst = (const unsigned *)S.nlist + nl_base(u, L, S.cap) + l;
+        unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
+        int q = 0;
+        for (int k = l; k < nn; k += 2 * L, q += 2) {
+            const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+            const float4 xa = __ldg(rel + nl_j(ea));
+            const float4 xb = __ldg(rel + nl_j(eb));
+            acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), dg, ga);
+            if (k + L < nn) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), dg, ga);
+            ea = na;
+            eb = nb;
         }
     }
 #pragma unroll
-    for (int g = 0; g < G; ++g) rho[g] = lane_sum<L>(rho[g]);
+    for (int g = 0; g < G; ++g) acc.rho[g] = lane_sum<L>(acc.rho[g]);
     if (valid && l == 0) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             if (g >= ga) continue;
-            const float fp = rho[g] > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho[g]) : 0.f;
+            const float rho = acc.rho[g];
+            const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
             ((float4 *)S.posfp)[a0 + g] = make_float4(ra[g].x, ra[g].y, ra[g].z, fp);
         }
     }
@@ -146,18 +184,15 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
     const int l = threadIdx.x % L;
     const bool valid = u < ctl->nunits;
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
-    const float rc2 = S.pot.f_rc2, pa = S.pot.f_a, rc = S.pot.f_rc, h = S.f_h;
-    const float An = S.pot.f_An, Bn = S.pot.f_Bn, Bm = S.pot.f_Bm, eps = S.pot.f_eps;
-    const int n = S.pot.n, m = S.pot.m;
-    const float fn = (float)n, fm = (float)m;
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
     int a0 = 0, ga = 0;
     if (valid) unit_atoms(S, u, a0, ga);
-    float fx[G], fy[G], fz[G], en[G];
+    ForceAcc<G, SC76> acc;
     float4 ra[G];
     float3 dg[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        fx[g] = fy[g] = fz[g] = en[g] = 0.f;
+        acc.fx[g] = acc.fy[g] = acc.fz[g] = acc.en[g] = 0.f;
         ra[g] = make_float4(0, 0, 0, 0);
         dg[g] = make_float3(0, 0, 0);
     }
@@ -165,77 +200,55 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (g < ga) ra[g] = lf[a0 + g];
-        if (G > 1 && ga > 1) {
+        if (G > 1 && ga > 1)
             dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
-        }
         const int nn = S.nn[u];
-        const int *__restrict__ lst = S.nlist + nl_base(u, L, S.cap);
+        const unsigned *__restrict__ lst = (const unsigned *)S.nlist + nl_base(u, L, S.cap) + l;
+        unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
         int q = 0;
-        int e1 = (l < nn) ? __ldg(lst + l) : a0;
-        int e2 = (L + l < nn) ? __ldg(lst + 32 + l) : a0;
-        float4 rn = __ldg(lf + (e1 & NL_JMASK));
-        for (int k = l; k < nn; k += L, ++q) {
-            const float4 lj = rn;
-            const unsigned code = (unsigned)e1 >> NL_JBITS;
-            const int e3 = (k + 2 * L < nn) ? __ldg(lst + (q + 2) * 32 + l) : a0;
-            rn = __ldg(lf + (e2 & NL_JMASK));
-            e1 = e2;
-            e2 = e3;
-            const float dx = fmaf(nl_off(code), h, lj.x - ra[0].x);
-            const float dy = fmaf(nl_off(code >> 3), h, lj.y - ra[0].y);
-            const float dz = fmaf(nl_off(code >> 6), h, lj.z - ra[0].z);
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float ex = dx - dg[g].x, ey = dy - dg[g].y, ez = dz - dg[g].z;
-                const float r2 = ex * ex + ey * ey + ez * ez;
-                if (r2 < rc2 && r2 > 0.f && g < ga) {
-                    const float ir = rsqrtf(r2);
-                    const float r = r2 * ir;
-                    const float s = pa * ir;
-                    float sn, sm;
-                    PowF<SC76>::pw(s, n, m, sn, sm);
-                    const float dphn = -fn * sn * ir + Bn;
-                    const float dphm = -fm * sm * ir + Bm;
-                    const float gg = (eps * dphn + (ra[g].w + lj.w) * dphm) * ir;
-                    fx[g] += gg * ex;
-                    fy[g] += gg * ey;
-                    fz[g] += gg * ez;
-                    en[g] += sn - An + Bn * (r - rc);
-                }
-            }
+        for (int k = l; k < nn; k += 2 * L, q += 2) {
+            const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+            const float4 xa = __ldg(lf + nl_j(ea));
+            const float4 xb = __ldg(lf + nl_j(eb));
+            acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), xa.w, dg, ra, ga);
+            if (k + L < nn) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), xb.w, dg, ra, ga);
+            ea = na;
+            eb = nb;
         }
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        fx[g] = lane_sum<L>(fx[g]);
-        fy[g] = lane_sum<L>(fy[g]);
-        fz[g] = lane_sum<L>(fz[g]);
-        en[g] = lane_sum<L>(en[g]);
+        acc.fx[g] = lane_sum<L>(acc.fx[g]);
+        acc.fy[g] = lane_sum<L>(acc.fy[g]);
+        acc.fz[g] = lane_sum<L>(acc.fz[g]);
+        acc.en[g] = lane_sum<L>(acc.en[g]);
     }
+    const float eps = S.pot.f_eps;
     float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f;
     if (valid && l == 0) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int a = a0 + g;
             if (g >= ga) continue;
+            const float fx = acc.fx[g], fy = acc.fy[g], fz = acc.fz[g];
             const float fpa = ra[g].w;
-            const float pe_a = 0.5f * eps * en[g] + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
+            const float pe_a = 0.5f * eps * acc.en[g] + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
             pe += pe_a;
             const uint8_t flag = S.flags[a];
-            if (flag == FLAG_RIGHT) rr -= (S.axis == 0 ? fx[g] : (S.axis == 1 ? fy[g] : fz[g]));
+            if (flag == FLAG_RIGHT) rr -= (S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
             float4 v = ((const float4 *)S.vel)[a];
             if (mode == MODE_EVAL) {
                 ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
                 double4_32a *o = (double4_32a *)S.eval_out;
-                o[S.orig[a]] = make_double4_32a(fx[g], fy[g], fz[g], pe_a);
+                o[S.orig[a]] = make_double4_32a(fx, fy, fz, pe_a);
                 continue;
             }
             const float kh = S.f_acc_half;
             if (phase == PH_RUN) {
                 if (flag == FLAG_MOBILE) {
-                    v.x += fx[g] * kh;
-                    v.y += fy[g] * kh;
-                    v.z += fz[g] * kh;
+                    v.x += fx * kh;
+                    v.y += fy * kh;
+                    v.z += fz * kh;
                 }
                 ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
@@ -244,9 +257,9 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
             const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
             if (start && flag == FLAG_MOBILE) {
-                v.x += fx[g] * kh;
-                v.y += fy[g] * kh;
-                v.z += fz[g] * kh;
+                v.x += fx * kh;
+                v.y += fy * kh;
+                v.z += fz * kh;
                 const float dt = S.f_dt;
                 qq[0] += v.x * dt;
                 qq[1] += v.y * dt;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__
         const int nn = S.nn[a];
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
         for (int k = l; k < nn; k += L) {
-            const int j = lst[(k / L) * 32 + (k % L)] & NL_JMASK;
+            const int j = nl_j((unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pos[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r = sqrt((dx * dx + dy * dy) + dz * dz);
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
         const int nn = S.nn[a];
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
         for (int k = l; k < nn; k += L) {
-            const int j = lst[(k / L) * 32 + (k % L)] & NL_JMASK;
+            const int j = nl_j((unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pf[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r = sqrt((dx * dx + dy * dy) + dz * dz);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -246,7 +247,7 @@ static PotDev make_pot(const pta_potential &p) {
 // ---------------------------------------------------------------------------
 struct Sizes {
     long long n, nunits;
-    int L, G, cap, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
+    int L, G, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
     double h, org[3];
     size_t list_words;
     long long series_cap;
@@ -278,15 +279,18 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     z->nunits = z->n;  // capacity; G = 2 sets the exact count at every build (below)
     const double rl = p.rc + par.skin;
     if (par.neigh_cap > 0) {
-        z->cap = (int)round_up((size_t)par.neigh_cap, 32);
+        z->cap_use = (int)round_up((size_t)par.neigh_cap, 32);
     } else {
         // atoms of one unit lie within ~3 A of each other: the union list
         // covers a sphere about 1.6 A wider
         const double dens = 4.0 / (s.a0 * s.a0 * s.a0);
         const double rr = rl + (z->G > 1 ? 1.6 : 0.0);
         const double nb = 4.0 / 3.0 * 3.141592653589793 * rr * rr * rr * dens;
-        z->cap = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
+        z->cap_use = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
     }
+    // four spare iterations per unit: the pair loops read entries ahead
+    // without bounds tests (spare entries hold earlier, valid indices or 0)
+    z->cap = z->cap_use + 4 * z->L;
     z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
     // cell edge a multiple of 2^-11 A and grid origin on the 2^-12 A grid, so
@@ -410,7 +414,15 @@ static void runner_free(Runner *r) {
 // them.  With `timed`, event-record nodes bracket the parts of each
 // iteration (events cannot sit inside a conditional body, so the build
 // time is measured around the whole conditional).
+static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool timed);
+
 static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed = false) {
+    // Nsight Compute cannot profile kernel nodes of graphs that hold
+    // conditional nodes; PTA_GRAPH_FLAT=1 captures the same kernels without
+    // one (the build kernels then return at once on the device when no
+    // build is needed)
+    const char *flat = std::getenv("PTA_GRAPH_FLAT");
+    if (flat && flat[0] == '1') return capture_iters_flat(r, iters, out, timed);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     std::vector<cudaGraphConditionalHandle> handles(iters);
@@ -475,6 +487,32 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
     if (e != cudaSuccess || rc != PTA_OK) {
         cudaGetLastError();
         cudaGraphDestroy(g);
+        return PTA_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PTA_ECUDA;
+    }
+    return PTA_OK;
+}
+
+static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool timed) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < iters; ++i) {
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
+        launch_rebuild(r->tab, 0, r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
+        launch_density(r->tab, 0, r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 2], r->cap, cudaEventRecordExternal);
+        launch_force(r->tab, MODE_STEP, r->cap);
+        if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 3], r->cap, cudaEventRecordExternal);
+    }
+    cudaError_t e = cudaStreamEndCapture(r->cap, &g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         return PTA_ECUDA;
     }
     e = cudaGraphInstantiate(out, g, 0);
@@ -957,6 +995,7 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.prec = c->par.precision;
     s.axis = c->spec.load_axis;
     s.cap = z.cap;
+    s.cap_use = z.cap_use;
     s.nblk_pair = z.nblk_pair;
     s.nblk_atom = z.nblk_atom;
     s.nblk_cell = z.nblk_cell;
@@ -972,6 +1011,8 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.inv_h = 1.0 / z.h;
     s.f_inv_h = (float)s.inv_h;
     s.f_h = (float)z.h;
+    s.f_h8 = (float)(z.h / 8.0);
+    s.f_h64 = (float)(z.h / 64.0);
     s.ncell = z.ncell;
     const double rl = c->pot.rc + c->par.skin;
     s.rl2 = rl * rl;
@@ -1230,7 +1271,7 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
             const int64_t a = a0 + g;
             row.clear();
             for (int k = 0; k < nn[u]; ++k) {
-                const int j = raw[(size_t)nl_index((int)u, k, s.L, s.cap)] & NL_JMASK;
+                const int j = nl_j((unsigned)raw[(size_t)nl_index((int)u, k, s.L, s.cap)]);
                 if (s.G > 1) {
                     // the same FP64 predicate as the list build (no contraction)
                     if (j == a) continue;

@@ -68,7 +68,8 @@ struct SpecCtl {
 
 struct SpecDev {
     // sizes
-    int n, L, prec, axis, cap;
+    int n, L, prec, axis, cap;   // cap: list stride per unit (usable entries: cap_use)
+    int cap_use;
     int G, nunits;             // atoms per unit (one thread group and one list per unit);
                                // nunits is the capacity (units in use: SpecCtl::nunits)
     int blk_pair0, nblk_pair;  // pair kernels: TPB/L units per block
@@ -85,7 +86,7 @@ struct SpecDev {
     int ncell;
     // list radius (rc + skin)^2 and its FP32 bracket; half skin squared
     double rl2;
-    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h, f_h;
+    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h, f_h, f_h8, f_h64;
     float f_org[3];
     PotDev pot;
     // integration constants
@@ -135,23 +136,31 @@ struct Tab {
     Group grp[8];
 };
 
-// Verlet-list entry (one list per unit of G consecutive atoms): neighbour
-// index in the low 23 bits, the neighbour's cell offset (dx, dy, dz) relative
-// to the cell of the unit's first atom in the high 9 bits, 3 bits per axis
-// holding d + 3.  With cell centres and the cell edge h on exact grids,
+// Verlet-list entry (one list per unit): neighbour index in the high 23
+// bits, the neighbour's cell offset (dx, dy, dz) relative to the cell of the
+// unit's first atom in the low 9 bits, 3 bits per axis holding d + 3.  With
+// cell centres and the cell edge h on exact grids,
 // r_j - r_i = (rel_j - rel_i) + h * d.
-constexpr int NL_JBITS = 23;
-constexpr int NL_JMASK = (1 << NL_JBITS) - 1;
-constexpr int MAX_ATOMS = 1 << NL_JBITS;
+constexpr int NL_CODE_BITS = 9;
+constexpr int MAX_ATOMS = 1 << 23;
 
-__host__ __device__ __forceinline__ int nl_code(int dx, int dy, int dz) {
-    return (dx + 3) | ((dy + 3) << 3) | ((dz + 3) << 6);
+__host__ __device__ __forceinline__ unsigned nl_entry(int j, int dx, int dy, int dz) {
+    return ((unsigned)j << NL_CODE_BITS) | (unsigned)((dx + 3) | ((dy + 3) << 3) | ((dz + 3) << 6));
 }
+__host__ __device__ __forceinline__ int nl_j(unsigned e) { return (int)(e >> NL_CODE_BITS); }
 
-// FP32 value (bits & 7) - 3, without an integer conversion: 0x4B400000 is
-// 1.5 * 2^23, whose last mantissa bits take small integers exactly
-__device__ __forceinline__ float nl_off(unsigned bits) {
-    return __int_as_float(0x4B400000 | (int)(bits & 7u)) - 12582915.0f;
+// The three offsets as exact FP32 multiples of the axis field, without
+// integer conversion: OR-ing a field into the mantissa of 1.5 * 2^23
+// (0x4B400000) gives 1.5 * 2^23 + field exactly.  x: (d + 3), y: 8 (d + 3),
+// z: 64 (d + 3); the caller scales by h, h / 8 and h / 64.
+__device__ __forceinline__ float nl_offx(unsigned e) {
+    return __int_as_float(0x4B400000 | (int)(e & 0x7u)) - 12582915.0f;
+}
+__device__ __forceinline__ float nl_offy(unsigned e) {
+    return __int_as_float(0x4B400000 | (int)(e & 0x38u)) - 12582936.0f;
+}
+__device__ __forceinline__ float nl_offz(unsigned e) {
+    return __int_as_float(0x4B400000 | (int)(e & 0x1C0u)) - 12583104.0f;
 }
 
 // Cells are numbered along a serpentine path (x reverses on every other row,
