@@ -8,7 +8,7 @@ FP64 accumulators) and the coarse-step update.  The metric is atom-steps/s
 (atoms x fine steps per second), whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pta|reference]
-                    [--workload large|plain|batched|uneven|served]
+                    [--workload large|plain|batched|uneven|served|precision]
 
 Under torchrun (N > 1) every rank advances its own specimen (independent
 replicas, no collective on the data path); the time is the maximum over
@@ -60,6 +60,9 @@ WORKLOADS = {
                         "tension or compression p=0.5, target strain 0.05..0.15, admitted by "
                         "memory footprint; one bench step = one tick (a coarse step of every "
                         "live specimen, 3 x 2,000 fine steps)"),
+    "precision": dict(name="precision_by_size", n_cells=None, T0=300.0, rate=None, burst=1000,
+                      precision=1, count=7,
+                      desc="mixed precision vs FP64 per size (10..49 cells), same seed"),
     "uneven": dict(name="uneven_28x_n10_49", n_cells=None, T0=300.0, rate=None, burst=2000,
                    precision=1, count=28,
                    desc="4 cubes each of 10,15,20,25,30,40,49 cells (3,786,384 atoms), "
@@ -258,6 +261,45 @@ def run_served(args, wl):
     eng.close()
     for s in list(sched.live.values()):
         s["handle"].close()
+    return out
+
+
+def run_precision(args, wl):
+    """Mixed precision against FP64, per specimen size (both on the GPU from
+    the same seed): relative differences of the burst means of K, U, T, the
+    differences in units of their combined standard error, and the per-atom
+    force error on identical positions."""
+    import torch
+    import paper_2603_07321_gb300 as P
+    P.build()
+    torch.cuda.set_device(0)
+    rows = []
+    for n in (10, 15, 20, 25, 30, 40, 49):
+        c64 = P.Ctx(n, T0=300.0, seed=11, precision=P.PREC_FP64)
+        c32 = P.Ctx(n, T0=300.0, seed=11, precision=P.PREC_MIXED)
+        pos, vel = c64.get_state()
+        c32.set_state(pos, vel)   # identical start
+        f64, _, _ = c64.forces()
+        f32, _, _ = c32.forces()
+        scale = np.sqrt(np.mean(np.sum(f64 ** 2, axis=1)))
+        ferr = float(np.max(np.linalg.norm(f32 - f64, axis=1)) / scale)
+        for c in (c64, c32):
+            c.apply_strain(1e-3)
+        steps = args.prec_steps
+        a64 = c64.fine_burst(steps)
+        a32 = c32.fine_burst(steps)
+        rel = [abs(a32.mean[q] - a64.mean[q]) / abs(a64.mean[q]) for q in range(3)]
+        z = [abs(a32.mean[q] - a64.mean[q]) / max(np.hypot(a32.se[q], a64.se[q]), 1e-300)
+             for q in range(3)]
+        rows.append({"n_cells": n, "atoms": c64.n, "force_err_rel_rms": ferr,
+                     "mean_rel_diff": {"K": rel[0], "U": rel[1], "T": rel[2]},
+                     "diff_in_se": {"K": z[0], "U": z[1], "T": z[2]},
+                     "fp64": list(a64.mean), "mixed": list(a32.mean)})
+        c64.close()
+        c32.close()
+    out = {"metric": "mixed-vs-fp64 slow-variable error", "workload": "precision_by_size",
+           "burst_steps": args.prec_steps, "rows": rows}
+    print(json.dumps(out), flush=True)
     return out
 
 
@@ -472,6 +514,8 @@ def main():
     ap.add_argument("--impl", default="pta", choices=["pta", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--prec-steps", type=int, default=1000,
+                    help="burst length of the precision comparison")
     ap.add_argument("--ref-sample", type=int, default=4,
                     help="fine steps per reference-arm step")
     args = ap.parse_args()
@@ -482,6 +526,8 @@ def main():
         run_reference(args, wl)
     elif args.workload == "served":
         run_served(args, wl)
+    elif args.workload == "precision":
+        run_precision(args, wl)
     else:
         run_pta(args, wl)
 

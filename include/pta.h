@@ -118,18 +118,27 @@ typedef struct {
     int atoms_per_thread; /* atoms sharing one neighbour list and thread group in
                            the mixed-precision kernels: 0 = automatic, 1 or 2
                            (2 needs lanes 1 or 2; FP64 uses 1)                 */
+    double prune_margin;  /* mixed precision: the pair passes read an inner list
+                           of the pairs within rc + prune_margin, pruned from the
+                           Verlet list whenever an atom has moved more than
+                           prune_margin / 2 since the last pruning; it holds every
+                           pair within rc in the same order, so results do not
+                           change.  0 = default 0.3 A, < 0 = off               */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
  * full step (the initial state is not sampled), standard errors from
  * non-overlapping blocks of block_steps samples (NaN with fewer than two
- * blocks), the number of neighbour-list builds during the burst. */
+ * blocks), the number of neighbour-list builds and inner-list prunings
+ * during the burst. */
 typedef struct {
     double mean[3];
     double se[3];
     int64_t nsteps;
     int32_t rebuilds;
     int32_t status; /* pta_status of this burst */
+    int32_t prunes; /* inner-list prunings during the burst (mixed precision) */
+    int32_t pad;
 } pta_averages;
 
 /* Coarse step t -> t+h.  v_pred: Eq. (pta_pred); v_d: Eq. (simp); e_v:

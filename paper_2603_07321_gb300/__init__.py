@@ -68,17 +68,18 @@ class Params(ctypes.Structure):
                 ("tol_j", ctypes.c_double * 3), ("floor", ctypes.c_double * 3),
                 ("burst_steps", ctypes.c_int64), ("block_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("neigh_cap", ctypes.c_int),
-                ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int)]
+                ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
+                ("prune_margin", ctypes.c_double)]
 
 
 class Averages(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double * 3), ("se", ctypes.c_double * 3),
                 ("nsteps", ctypes.c_int64), ("rebuilds", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("prunes", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {"mean": list(self.mean), "se": list(self.se), "nsteps": self.nsteps,
-                "rebuilds": self.rebuilds, "status": self.status}
+                "rebuilds": self.rebuilds, "prunes": self.prunes, "status": self.status}
 
 
 class CoarseResult(ctypes.Structure):

@@ -355,7 +355,10 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
 __global__ void k_build_done(const SpecDev *__restrict__ specs, int force) {
     const SpecDev &S = specs[blockIdx.x];
     if (!build_active(S, force)) return;
-    if (threadIdx.x == 0) S.ctl->list_L = S.L;
+    if (threadIdx.x == 0) {
+        S.ctl->list_L = S.L;
+        S.ctl->prune = 1;  // a fresh list is always pruned before use
+    }
 }
 
 __global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
@@ -364,14 +367,20 @@ __global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
     if (threadIdx.x == 0) S.ctl->max_nn = 0;
 }
 
-// one block: does any specimen of the table need a list build before its
-// next pair pass?  Sets the condition of the graph node that holds the build.
+// one block: does any specimen of the table need a list build, or only a
+// pruning of its inner list, before its next pair pass?  Sets the condition
+// of the graph node that holds that work (LIST_BUILD, LIST_PRUNE, LIST_NONE).
 __global__ void k_decide_rebuild(const SpecDev *__restrict__ specs, int nspec,
                                  cudaGraphConditionalHandle handle) {
-    int need = 0;
-    for (int s = threadIdx.x; s < nspec; s += blockDim.x) need |= build_active(specs[s], 0);
-    need = __syncthreads_or(need);
-    if (threadIdx.x == 0) cudaGraphSetConditional(handle, need ? 1u : 0u);
+    int build = 0, prune = 0;
+    for (int s = threadIdx.x; s < nspec; s += blockDim.x) {
+        build |= build_active(specs[s], 0);
+        prune |= prune_active(specs[s], 0);
+    }
+    build = __syncthreads_or(build);
+    prune = __syncthreads_or(prune);
+    if (threadIdx.x == 0)
+        cudaGraphSetConditional(handle, build ? LIST_BUILD : (prune ? LIST_PRUNE : LIST_NONE));
 }
 
 void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st) {

@@ -29,20 +29,21 @@ __device__ __forceinline__ T lane_sum(T v) {
 }
 
 // Called by every thread of a pair block after the warp reductions (values
-// valid in lane 0 of each warp).  Block partials go to S.part; the last
-// block of the specimen to finish sums all partials in a fixed order and
-// advances the specimen's control block:
+// valid in lane 0 of each warp).  Block partials go to S.part (8 doubles per
+// block); the last block of the specimen to finish sums all partials in a
+// fixed order and advances the specimen's control block:
 //   MODE_STEP, phase RUN:     sample (K, U, T) into the series, step count + 1,
 //                             burst over after nsteps samples
 //   MODE_STEP, phase REFRESH: forces refreshed and the first step started
 //   MODE_EVAL:                K, U, T stored in eval_obs
-// and in MODE_STEP the position buffers swap and the skin test sets the
-// rebuild flag.
+// and in MODE_STEP the position buffers swap, the skin test sets the
+// rebuild flag and the pruning margin test the prune flag.
 __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double pe_w, double rr_w,
-                                 double d2_w, int mode, int phase, long long done,
+                                 double d2_w, double dp2_w, int mode, int phase, long long done,
                                  long long nsteps) {
-    __shared__ double shw[4][TPB / 32];
-    __shared__ double red[4][TPB];
+    constexpr int NV = 5;  // K, U, R, max displacement^2 since the build and since the pruning
+    __shared__ double shw[NV][TPB / 32];
+    __shared__ double red[NV][TPB];
     __shared__ int is_last;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -50,21 +51,24 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
         shw[1][w] = pe_w;
         shw[2][w] = rr_w;
         shw[3][w] = d2_w;
+        shw[4][w] = dp2_w;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double k = 0, p = 0, r = 0, d = 0;
+        double k = 0, p = 0, r = 0, d = 0, e = 0;
         for (int i = 0; i < TPB / 32; ++i) {
             k = k + shw[0][i];
             p = p + shw[1][i];
             r = r + shw[2][i];
             d = fmax(d, shw[3][i]);
+            e = fmax(e, shw[4][i]);
         }
-        double *P = S.part + 4LL * lb;
+        double *P = S.part + 8LL * lb;
         P[0] = k;
         P[1] = p;
         P[2] = r;
         P[3] = d;
+        P[4] = e;
         __threadfence();
         const unsigned prev = atomicAdd(&S.ctl->blocks_done, 1u);
         is_last = (prev == (unsigned)(S.nblk_pair - 1));
@@ -72,18 +76,16 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double k = 0, p = 0, r = 0, d = 0;
+    double v[NV] = {0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < S.nblk_pair; b += TPB) {
-        const double *P = S.part + 4LL * b;
-        k = k + __ldcg(P);
-        p = p + __ldcg(P + 1);
-        r = r + __ldcg(P + 2);
-        d = fmax(d, __ldcg(P + 3));
+        const double *P = S.part + 8LL * b;
+        v[0] = v[0] + __ldcg(P);
+        v[1] = v[1] + __ldcg(P + 1);
+        v[2] = v[2] + __ldcg(P + 2);
+        v[3] = fmax(v[3], __ldcg(P + 3));
+        v[4] = fmax(v[4], __ldcg(P + 4));
     }
-    red[0][threadIdx.x] = k;
-    red[1][threadIdx.x] = p;
-    red[2][threadIdx.x] = r;
-    red[3][threadIdx.x] = d;
+    for (int q = 0; q < NV; ++q) red[q][threadIdx.x] = v[q];
     __syncthreads();
     for (int s = TPB / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
@@ -91,12 +93,14 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
             red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + s];
             red[2][threadIdx.x] = red[2][threadIdx.x] + red[2][threadIdx.x + s];
             red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+            red[4][threadIdx.x] = fmax(red[4][threadIdx.x], red[4][threadIdx.x + s]);
         }
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
     SpecCtl *c = S.ctl;
-    const double K = red[0][0], U = red[1][0], T = red[2][0] * S.t_fac, md2 = red[3][0];
+    const double K = red[0][0], U = red[1][0], T = red[2][0] * S.t_fac, md2 = red[3][0],
+                 mp2 = red[4][0];
     if (mode == MODE_EVAL) {
         c->eval_obs[0] = K;
         c->eval_obs[1] = U;
@@ -122,6 +126,7 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
             c->phase = PH_RUN;
         }
         c->rebuild = (md2 > (double)S.half_skin2) ? 1 : 0;
+        if (S.prune_on && mp2 > (double)S.half_prune2) c->prune = 1;
         c->parity ^= 1;
     }
     __threadfence();

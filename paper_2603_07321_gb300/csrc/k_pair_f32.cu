@@ -59,6 +59,19 @@ struct PowF {
 // the four spare iterations every list keeps, whose entries are valid
 // indices, so the loop carries no bounds tests.
 
+// the entries lane l of unit u reads (the inner list when pruning is on, else
+// the Verlet list), as a pointer to its first word (stride 32) and a count
+__device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, int l, int L, int &cl) {
+    const long long off = nl_base(u, L, S.cap) + l;
+    if (S.prune_on) {
+        cl = S.pnn[(long long)u * L + l];
+        return (const unsigned *)S.plist + off;
+    }
+    const int nn = S.nn[u];
+    cl = nn > l ? (nn - l + L - 1) / L : 0;
+    return (const unsigned *)S.nlist + off;
+}
+
 // displacement of entry e's atom (record x) from the unit's first atom (record r0)
 __device__ __forceinline__ float3 entry_disp(unsigned e, float4 x, float4 r0, float h, float h8,
                                              float h64) {
@@ -142,16 +155,15 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             if (g < ga) ra[g] = rel[a0 + g];
         if (G > 1 && ga > 1)  // both atoms share a cell: the offset is rel_1 - rel_0
             dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
-        const int nn = S.nn[u];
-        const unsigned *__restrict__ lst = (const unsigned *)S.nlist + nl_base(u, L, S.cap) + l;
+        int cl;
+        const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
-        int q = 0;
-        for (int k = l; k < nn; k += 2 * L, q += 2) {
+        for (int q = 0; q < cl; q += 2) {
             const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
             const float4 xa = __ldg(rel + nl_j(ea));
             const float4 xb = __ldg(rel + nl_j(eb));
             acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), dg, ga);
-            if (k + L < nn) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), dg, ga);
+            if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), dg, ga);
             ea = na;
             eb = nb;
         }
@@ -202,16 +214,15 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             if (g < ga) ra[g] = lf[a0 + g];
         if (G > 1 && ga > 1)
             dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
-        const int nn = S.nn[u];
-        const unsigned *__restrict__ lst = (const unsigned *)S.nlist + nl_base(u, L, S.cap) + l;
+        int cl;
+        const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
-        int q = 0;
-        for (int k = l; k < nn; k += 2 * L, q += 2) {
+        for (int q = 0; q < cl; q += 2) {
             const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
             const float4 xa = __ldg(lf + nl_j(ea));
             const float4 xb = __ldg(lf + nl_j(eb));
             acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), xa.w, dg, ra, ga);
-            if (k + L < nn) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), xb.w, dg, ra, ga);
+            if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), xb.w, dg, ra, ga);
             ea = na;
             eb = nb;
         }
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
         acc.en[g] = lane_sum<L>(acc.en[g]);
     }
     const float eps = S.pot.f_eps;
-    float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f;
+    float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f, dp2 = 0.f;
     if (valid && l == 0) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -285,13 +296,113 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             const float ex = (hh[0] - rf.x) + qq[0], ey = (hh[1] - rf.y) + qq[1],
                         ez = (hh[2] - rf.z) + qq[2];
             d2 = fmaxf(d2, ex * ex + ey * ey + ez * ez);
+            if (S.prune_on) {
+                const float4 pf = S.pref[a];
+                const float px = (hh[0] - pf.x) + qq[0], py = (hh[1] - pf.y) + qq[1],
+                            pz = (hh[2] - pf.z) + qq[2];
+                dp2 = fmaxf(dp2, px * px + py * py + pz * pz);
+            }
         }
     }
     ke = warp_sum(ke);
     pe = warp_sum(pe);
     rr = warp_sum(rr);
     d2 = warp_max(d2);
-    step_tail(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, mode, phase, done, nsteps);
+    dp2 = warp_max(dp2);
+    step_tail(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode, phase, done,
+              nsteps);
+}
+
+// Inner list: every lane keeps, in order, the entries of its own column of
+// the Verlet list that lie within the pruning radius of an atom of the unit
+// (FP32 distances tested against (rc + margin)^2 widened by 1e-5).  Pairs
+// within rc are therefore all kept, in the order the lane sums them.
+template <int L, int G>
+__global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict__ specs,
+                                                      const int *__restrict__ b2s, int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (S.prec == PTA_PREC_FP64 || !prune_active(S, force)) return;
+    const SpecCtl *ctl = S.ctl;
+    const int par = ctl->parity;
+    constexpr int UPB = TPB / L;
+    const int u = (blockIdx.x - S.blk_pair0) * UPB + threadIdx.x / L;
+    const int l = threadIdx.x % L;
+    if (u >= ctl->nunits) return;
+    const float4 *__restrict__ rel = S.rel[par];
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64, rp2 = S.f_rp2;
+    int a0, ga;
+    unit_atoms(S, u, a0, ga);
+    float4 ra[G];
+    float3 dg[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        ra[g] = make_float4(0, 0, 0, 0);
+        dg[g] = make_float3(0, 0, 0);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        if (g < ga) ra[g] = rel[a0 + g];
+    if (G > 1 && ga > 1)
+        dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+    const long long off = nl_base(u, L, S.cap) + l;
+    const unsigned *__restrict__ src = (const unsigned *)S.nlist + off;
+    unsigned *__restrict__ dst = (unsigned *)S.plist + off;
+    const int nn = S.nn[u];
+    int kept = 0;
+    for (int q = 0; q * L + l < nn; ++q) {
+        const unsigned e = __ldg(src + q * 32);
+        const float4 x = __ldg(rel + nl_j(e));
+        const float3 d = entry_disp(e, x, ra[0], h, h8, h64);
+        bool in = false;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ex = d.x - dg[g].x, ey = d.y - dg[g].y, ez = d.z - dg[g].z;
+            in |= (g < ga) && (ex * ex + ey * ey + ez * ez < rp2);
+        }
+        if (in) dst[(kept++) * 32] = e;
+    }
+    S.pnn[(long long)u * L + l] = kept;
+    if (l == 0) {
+        for (int g = 0; g < ga; ++g) {
+            const int a = a0 + g;
+            const float4 hi = ((const float4 *)S.pos[par])[a];
+            const float4 lo = S.lo[par][a];
+            S.pref[a] = make_float4(hi.x + lo.x, hi.y + lo.y, hi.z + lo.z, 0.f);
+        }
+    }
+}
+
+// after the pruning: clear the flag (a separate kernel, so that every block
+// of the pruning kernel reads the same flag)
+__global__ void k_prune_done(const SpecDev *__restrict__ specs, int force) {
+    const SpecDev &S = specs[blockIdx.x];
+    if (!prune_active(S, force)) return;
+    if (threadIdx.x == 0) {
+        S.ctl->prune = 0;
+        S.ctl->prunes += 1;
+    }
+}
+
+void launch_prune(const Tab &t, int force, cudaStream_t st) {
+    for (int i = 0; i < t.ngroups; ++i) {
+        const Group &g = t.grp[i];
+        if (g.nblk <= 0 || g.prec == PTA_PREC_FP64) continue;
+        if (g.G == 2) {
+            if (g.L == 1)
+                k_prune_f32<1, 2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force);
+            else
+                k_prune_f32<2, 2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force);
+        } else {
+            switch (g.L) {
+                case 1: k_prune_f32<1, 1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+                case 2: k_prune_f32<2, 1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+                case 4: k_prune_f32<4, 1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+                case 8: k_prune_f32<8, 1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+                default: k_prune_f32<16, 1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+            }
+        }
+    }
+    k_prune_done<<<t.nspec, 32, 0, st>>>(t.specs, force);
 }
 
 // ---------------------------------------------------------------------------

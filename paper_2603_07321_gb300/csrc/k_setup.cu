@@ -303,6 +303,7 @@ __global__ void k_burst_begin(const SpecDev *__restrict__ specs, const long long
     c->done = 0;
     c->sum[0] = c->sum[1] = c->sum[2] = 0.0;
     c->rebuilds = 0;
+    c->prunes = 0;
     c->blocks_done = 0;
     // a burst always starts from a fresh neighbour list, so its result does
     // not depend on when earlier lists were built (checkpoints, batching)
@@ -355,6 +356,8 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
         }
         r.nsteps = n;
         r.rebuilds = c->rebuilds;
+        r.prunes = c->prunes;
+        r.pad = 0;
         int e = c->err;
         r.status = (e & ERR_OVERFLOW) ? PTA_ENEIGH_OVERFLOW
                    : (e & ERR_NAN)    ? PTA_ENAN

@@ -248,6 +248,8 @@ static PotDev make_pot(const pta_potential &p) {
 struct Sizes {
     long long n, nunits;
     int L, G, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
+    int prune_on;
+    double prune_margin;
     double h, org[3];
     size_t list_words;
     long long series_cap;
@@ -278,6 +280,9 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     z->G = par.atoms_per_thread ? par.atoms_per_thread : 1;
     z->nunits = z->n;  // capacity; G = 2 sets the exact count at every build (below)
     const double rl = p.rc + par.skin;
+    z->prune_margin = par.prune_margin == 0.0 ? 0.3 : par.prune_margin;
+    z->prune_on = (par.precision == PTA_PREC_MIXED && z->prune_margin > 0.0 &&
+                   z->prune_margin < par.skin) ? 1 : 0;
     if (par.neigh_cap > 0) {
         z->cap_use = (int)round_up((size_t)par.neigh_cap, 32);
     } else {
@@ -346,12 +351,17 @@ static size_t footprint(const Sizes &z, int prec) {
     add(4 * n);                      // orig
     add(perm_layout(n, prec).total); // permutation scratch
     add(4 * z.list_words);           // nlist
+    if (z.prune_on) {
+        add(4 * z.list_words);       // plist
+        add(4 * (size_t)z.nunits * z.L);  // pnn
+        add(16 * n);                 // pref
+    }
     add(4 * (size_t)z.nunits);       // nn
     if (z.G == 2) {
         add(4 * n);                  // unit_first
         add(4 * ((size_t)z.ncell + 1));  // unit_cell
     }
-    add(32 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
+    add(64 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
     add(48 * n);                     // stage
@@ -380,6 +390,7 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
         (par->precision == PTA_PREC_FP64 || (par->lanes != 0 && par->lanes > 2)))
         return PTA_EUNSUPPORTED;
     if (par->neigh_cap < 0 || par->neigh_cap > 4096) return PTA_EINVAL;
+    if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
     if (n > (long long)MAX_ATOMS) return PTA_ERANGE;
     if (par->precision == PTA_PREC_MIXED) {
@@ -408,10 +419,10 @@ static void runner_free(Runner *r) {
 }
 
 // Graph of `iters` fine-step iterations.  Each iteration is
-//   [decide] -> IF(a list build is needed) { build kernels } -> density -> force
-// where the decide kernel sets the IF node's condition on the device, so
-// the build kernels are skipped without a launch when no specimen needs
-// them.  With `timed`, event-record nodes bracket the parts of each
+//   [decide] -> SWITCH { 0: build + prune kernels, 1: prune kernels } -> density -> force
+// where the decide kernel sets the switch value on the device (2 when no
+// specimen needs either), so list maintenance costs no launch on the steps
+// that need none.  With `timed`, event-record nodes bracket the parts of each
 // iteration (events cannot sit inside a conditional body, so the build
 // time is measured around the whole conditional).
 static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool timed);
@@ -427,7 +438,7 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
     CK(cudaGraphCreate(&g, 0));
     std::vector<cudaGraphConditionalHandle> handles(iters);
     for (int i = 0; i < iters; ++i)
-        if (cudaGraphConditionalHandleCreate(&handles[i], g, 0, cudaGraphCondAssignDefault) !=
+        if (cudaGraphConditionalHandleCreate(&handles[i], g, LIST_NONE, cudaGraphCondAssignDefault) !=
             cudaSuccess) {
             cudaGetLastError();
             cudaGraphDestroy(g);
@@ -452,30 +463,31 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
         cudaGraphNodeParams np = {};
         np.type = cudaGraphNodeTypeConditional;
         np.conditional.handle = handles[i];
-        np.conditional.type = cudaGraphCondTypeIf;
-        np.conditional.size = 1;
+        np.conditional.type = cudaGraphCondTypeSwitch;
+        np.conditional.size = 2;  // LIST_BUILD, LIST_PRUNE (LIST_NONE runs neither)
         cudaGraphNode_t cnode;
         if (cudaGraphAddNode(&cnode, cg, deps, edata, ndeps, &np) != cudaSuccess) {
             rc = PTA_ECUDA;
             break;
         }
-        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaGraph_t bodies[2] = {np.conditional.phGraph_out[0], np.conditional.phGraph_out[1]};
         if (cudaStreamUpdateCaptureDependencies(r->cap, &cnode, nullptr, 1,
                                                 cudaStreamSetCaptureDependencies) != cudaSuccess) {
             rc = PTA_ECUDA;
             break;
         }
-        if (cudaStreamBeginCaptureToGraph(r->cap2, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            rc = PTA_ECUDA;
-            break;
+        for (int b = 0; b < 2 && rc == PTA_OK; ++b) {
+            if (cudaStreamBeginCaptureToGraph(r->cap2, bodies[b], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                rc = PTA_ECUDA;
+                break;
+            }
+            if (b == (int)LIST_BUILD) launch_rebuild(r->tab, 0, r->cap2);
+            launch_prune(r->tab, 0, r->cap2);
+            cudaGraph_t bout = nullptr;
+            if (cudaStreamEndCapture(r->cap2, &bout) != cudaSuccess) rc = PTA_ECUDA;
         }
-        launch_rebuild(r->tab, 0, r->cap2);
-        cudaGraph_t bout = nullptr;
-        if (cudaStreamEndCapture(r->cap2, &bout) != cudaSuccess) {
-            rc = PTA_ECUDA;
-            break;
-        }
+        if (rc != PTA_OK) break;
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
         launch_density(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 2], r->cap, cudaEventRecordExternal);
@@ -504,6 +516,7 @@ static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool t
     for (int i = 0; i < iters; ++i) {
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
         launch_rebuild(r->tab, 0, r->cap);
+        launch_prune(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
         launch_density(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 2], r->cap, cudaEventRecordExternal);
@@ -944,12 +957,17 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     AL(orig, 4 * n, int *);
     AL(perm_tmp, perm_layout(n, c->par.precision).total, void *);
     AL(nlist, 4 * z.list_words, int *);
+    if (z.prune_on) {
+        AL(plist, 4 * z.list_words, int *);
+        AL(pnn, 4 * (size_t)z.nunits * z.L, int *);
+        AL(pref, 16 * n, float4 *);
+    }
     AL(nn, 4 * (size_t)z.nunits, int *);
     if (z.G == 2) {
         AL(unit_first, 4 * n, int *);
         AL(unit_cell, 4 * ((size_t)z.ncell + 1), int *);
     }
-    AL(part, 32 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
+    AL(part, 64 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
     AL(stage, 48 * n, double *);
@@ -1019,6 +1037,12 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.f_rl2_lo = (float)(s.rl2 * (1.0 - 1e-5));
     s.f_rl2_hi = (float)(s.rl2 * (1.0 + 1e-5));
     s.half_skin2 = (float)(0.25 * c->par.skin * c->par.skin);
+    s.prune_on = z.prune_on;
+    {
+        const double rp = c->pot.rc + z.prune_margin;
+        s.f_rp2 = (float)(rp * rp * (1.0 + 1e-5));
+        s.half_prune2 = (float)(0.25 * z.prune_margin * z.prune_margin);
+    }
     s.pot = make_pot(c->pot);
     s.mass = c->par.mass_amu;
     s.dt = c->par.dt_fs;
@@ -1201,6 +1225,7 @@ int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     Runner *r;
     CKR(ctx_solo(c, &r));
     launch_rebuild(r->tab, 1, c->stream);
+    launch_prune(r->tab, 1, c->stream);
     launch_density(r->tab, 1, c->stream);
     launch_force(r->tab, MODE_EVAL, c->stream);
     CKR(launch_check());

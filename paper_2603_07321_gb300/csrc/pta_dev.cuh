@@ -59,6 +59,8 @@ struct SpecCtl {
     int rebuilds;              // list builds in the current burst
     int max_nn;                // largest neighbour count at the last build
     int nunits;                // units in use (G = 2: pairs of atoms of one cell)
+    int prune;                 // 1: prune the inner list before the next pair pass
+    int prunes;                // prunings in the current burst
     double sum[3];             // running sums of K, U, T over the burst
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
@@ -110,6 +112,10 @@ struct SpecDev {
     int *unit_cell;   // G = 2: first unit of each cell (ncell + 1)
     void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
     int *nlist, *nn;
+    int *plist, *pnn;   // inner list (same layout as nlist), entries per unit and lane
+    float4 *pref;       // positions at the last pruning
+    int prune_on;
+    float f_rp2, half_prune2;
     double *part;       // per pair block: K, U, R, max displacement^2
     double *series;     // series_cap x 3 samples of the current burst
     long long series_cap;
@@ -254,7 +260,16 @@ void launch_burst_end(const Tab &t, int slot, pta_averages *out, cudaStream_t st
 void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
 void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
 void launch_rebuild(const Tab &t, int force, cudaStream_t st);
+void launch_prune(const Tab &t, int force, cudaStream_t st);
 void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st);
+// list maintenance decided on the device: 0 build + prune, 1 prune, 2 nothing
+constexpr unsigned LIST_BUILD = 0, LIST_PRUNE = 1, LIST_NONE = 2;
+
+__device__ __forceinline__ bool prune_active(const SpecDev &S, int force) {
+    if (!S.prune_on) return false;
+    if (force) return true;
+    return S.ctl->phase != PH_IDLE && S.ctl->prune != 0;
+}
 void launch_density(const Tab &t, int force, cudaStream_t st);
 void launch_force(const Tab &t, int mode, cudaStream_t st);
 

@@ -83,9 +83,14 @@ def test_footprint(P):
     f10 = P.pta_footprint_bytes(P.make_specimen(10), p64)
     f20 = P.pta_footprint_bytes(P.make_specimen(20), p64)
     assert 0 < f10 < f20
-    assert P.pta_footprint_bytes(P.make_specimen(20), pmx) < f20
-    # about 1-2 KB per atom at the default list capacity
-    assert 500 < f20 / (4 * 20 ** 3) < 4000
+    fmx = P.pta_footprint_bytes(P.make_specimen(20), pmx)
+    # mixed precision keeps a second (pruned) list: more list memory, less state
+    nomx = P.pta_footprint_bytes(P.make_specimen(20), P.default_params(precision=1,
+                                                                      prune_margin=-1.0))
+    assert nomx < fmx and nomx < f20
+    # about 1-4 KB per atom at the default list capacity
+    for f in (f20, fmx):
+        assert 500 < f / (4 * 20 ** 3) < 4000
     bad = P.make_specimen((2, 2, 2))
     assert P.pta_footprint_bytes(bad, p64) == 0
 

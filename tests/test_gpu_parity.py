@@ -297,3 +297,19 @@ def test_kernel_timing_records_every_iteration(P, oracle):
     assert np.array_equal(ctx.series(), ctx2.series())
     ctx.close()
     ctx2.close()
+
+
+def test_pruned_inner_list_changes_no_result(P, oracle):
+    # the inner list holds every pair within rc in the same per-lane order:
+    # trajectories with and without it are bit-identical
+    out = []
+    for margin in (0.3, -1.0):
+        ctx = P.Ctx((8, 7, 9), T0=300.0, seed=12, precision=P.PREC_MIXED, lanes=2,
+                    prune_margin=margin)
+        ctx.apply_strain(2e-3)
+        a = ctx.fine_burst(300)
+        out.append((ctx.series().copy(), ctx.get_state(), a.prunes))
+        ctx.close()
+    assert out[0][2] > 1 and out[1][2] == 0
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1][0], out[1][1][0])
