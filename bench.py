@@ -70,6 +70,25 @@ WORKLOADS = {
 }
 
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+
+
+def captured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed Nsight Compute
+    summary, or None when the summary is missing or the kernel's source has
+    changed since it was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    src = os.path.join(ROOT, "paper_2603_07321_gb300", "csrc", "k_pair_f32.cu")
+    try:
+        txt = open(path).read()
+        vals = dict(line.split(": ", 1) for line in txt.splitlines()
+                    if line.startswith(("dram_bytes_per_launch:", "kernel_source_sha256_16:")))
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if vals.get("kernel_source_sha256_16", "").strip() != cur:
+            return None
+        return int(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 N_SM = 152
 
 
@@ -372,10 +391,18 @@ def run_pta(args, wl):
     dominant = ("force", ach_force, force_ms) if force_ms >= dens_ms else ("density", ach_dens,
                                                                            dens_ms)
 
-    # launches of this library's kernels in the timed region
+    # launches of this library's kernels in the timed region: per fine-step
+    # iteration the decide kernel and, per (precision, lanes) group, the
+    # density and force passes; per list build 11 kernels; per pruning one
+    # kernel per group and one bookkeeping kernel; per burst the grip
+    # increment, burst start and burst end; per coarse step the update
+    groups = len({(c.params.precision, c.layout()["lanes"], c.layout()["atoms_per_thread"])
+                  for c in ctxs})
+    builds = sum(b.rebuilds for step in results for r in step for b in r.burst)
+    prunes = sum(b.prunes for step in results for r in step for b in r.burst)
     bursts = 3 * args.steps
-    groups = len({(c.params.precision, 0) for c in ctxs})
-    launches = int(kt.iterations * (7 + 2 * groups) + bursts * 3 + args.steps)
+    launches = int(kt.iterations * (1 + 2 * groups) + builds * 11 + prunes * (groups + 1)
+                   + bursts * 3 + args.steps)
 
     # end to end through the public API with host buffers: per step the state
     # goes host -> device from pinned memory, the coarse step runs, and the
@@ -425,7 +452,9 @@ def run_pta(args, wl):
             "roofline": {"bound": "alu", "kernel": "k_%s_f32" % dominant[0]
                          if wl["precision"] == 1 else "k_%s_f64" % dominant[0],
                          "achieved": dominant[1], "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": dominant[1] / peak_tflops, "traffic": None,
+                         "frac": dominant[1] / peak_tflops,
+                         "traffic": captured_traffic("k_%s_f32" % dominant[0], wl["name"])
+                         if wl["precision"] == 1 else None,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz "
                                         "(recipe unit counts, measured max clock)" % clk,
                          "launch_ms": dominant[2],

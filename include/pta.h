@@ -194,6 +194,10 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0_K, 
 void pta_destroy(pta_ctx *ctx);
 
 int pta_natoms(const pta_ctx *ctx, int64_t *n);
+/* The kernel layout chosen for this context: out[0] threads per atom
+ * (lanes), out[1] atoms per thread group, out[2] neighbour-list capacity per
+ * atom, out[3] 1 when the pruned inner list is in use. */
+int pta_get_layout(const pta_ctx *ctx, int32_t out[4]);
 /* 0 mobile, 1 left grip, 2 right grip; n must equal the atom count */
 int pta_get_flags(pta_ctx *ctx, uint8_t *flags, int64_t n);
 

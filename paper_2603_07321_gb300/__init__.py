@@ -119,6 +119,7 @@ _SIGS = {
                                   _P(Params), _VP, _P(_VP)]),
     "pta_destroy": (None, [_VP]),
     "pta_natoms": (ctypes.c_int, [_VP, _P(ctypes.c_int64)]),
+    "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_flags": (ctypes.c_int, [_VP, _P(ctypes.c_uint8), ctypes.c_int64]),
     "pta_apply_strain": (ctypes.c_int, [_VP, ctypes.c_double]),
     "pta_get_strain": (ctypes.c_int, [_VP, _P(ctypes.c_double)]),
@@ -269,6 +270,13 @@ def pta_natoms(h) -> int:
     n = ctypes.c_int64()
     _check(load().pta_natoms(h, ctypes.byref(n)), "pta_natoms")
     return n.value
+
+
+def pta_get_layout(h) -> dict:
+    out = (ctypes.c_int32 * 4)()
+    _check(load().pta_get_layout(h, out), "pta_get_layout")
+    return {"lanes": out[0], "atoms_per_thread": out[1], "neigh_cap": out[2],
+            "pruned_list": bool(out[3])}
 
 
 def pta_get_flags(h, n):
@@ -458,6 +466,9 @@ class Ctx:
 
     def flags(self):
         return pta_get_flags(self.h, self.n)
+
+    def layout(self):
+        return pta_get_layout(self.h)
 
     def apply_strain(self, d_eps):
         pta_apply_strain(self.h, d_eps)

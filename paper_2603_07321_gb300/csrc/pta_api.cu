@@ -1117,6 +1117,15 @@ static int fetch_orig(pta_ctx *c, std::vector<int> &orig) {
     return PTA_OK;
 }
 
+int pta_get_layout(const pta_ctx *c, int32_t out[4]) {
+    if (!c || !out) return PTA_EINVAL;
+    out[0] = c->hd.L;
+    out[1] = c->hd.G;
+    out[2] = c->hd.cap_use;
+    out[3] = c->hd.prune_on;
+    return PTA_OK;
+}
+
 int pta_get_flags(pta_ctx *c, uint8_t *flags, int64_t n) {
     if (!c || !flags || n != c->hd.n) return PTA_EINVAL;
     if (c->broken) return PTA_ECUDA;
