@@ -239,6 +239,23 @@ __global__ void k_unit_table(const SpecDev *__restrict__ specs, const int *__res
     S.unit_first[S.unit_cell[c] + r / 2] = p | ((r + 1 < cnt) ? UNIT_SECOND : 0);
 }
 
+// mixed precision: neighbour records of every atom relative to its new cell
+// (the build tests candidates with them, and the first density pass reads them)
+__global__ void k_rel_all(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                          int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (S.prec == PTA_PREC_FP64 || !build_active(S, force)) return;
+    const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
+    if (a >= S.n) return;
+    const int par = S.ctl->parity;
+    const float4 h = ((const float4 *)S.pos[par])[a];
+    const float4 l = S.lo[par][a];
+    const float3 C = cell_centre(S, S.atom_cell[a]);
+    S.rel[par][a] = make_float4((h.x - C.x) + l.x, (h.y - C.y) + l.y, (h.z - C.z) + l.z, 0.f);
+}
+
+constexpr int RW_ROWS = 48;
+
 // exact list predicate between atoms a and j (FP32 first; the FP64 test
 // decides only the thin band around the list radius)
 __device__ __forceinline__ bool in_list(const SpecDev &S, int par, bool mixed, int a, double xa,
@@ -277,7 +294,72 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
     const int u = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
     const int par = S.ctl->parity;
     int cnt = 0;
-    if (u < S.ctl->nunits) {
+    if (S.G == 1 && S.L == 1 && S.prec != PTA_PREC_FP64) {
+        // warp-uniform loop over the 27 cells around each atom's cell; the
+        // FP32 candidate test uses the cell-relative records, the FP64 test
+        // decides the thin band around the list radius; list rows are staged
+        // in shared memory and written whole
+        __shared__ int rowbuf[TPB / 32][RW_ROWS * 32];
+        const int lane = threadIdx.x & 31;
+        const int nu = S.ctl->nunits;
+        const bool valid = u < nu;
+        const int a = valid ? u : 0;
+        RowWriter<RW_ROWS> wr;
+        wr.buf = rowbuf[threadIdx.x >> 5];
+        wr.tile = S.nlist + nl_base(u - lane, 1, S.cap);
+        wr.lane = lane;
+        wr.flushed = 0;
+        wr.direct_from = 1 << 30;
+        for (int r = 0; r < RW_ROWS; ++r) wr.buf[r * 32 + lane] = (a << NL_CODE_BITS);  // valid filler
+        __syncwarp();
+        const float4 ra = S.rel[par][a];
+        const float4 ha = ((const float4 *)S.pos[par])[a];
+        const float4 la = S.lo[par][a];
+        const double xa = (double)ha.x + (double)la.x, ya = (double)ha.y + (double)la.y,
+                     za = (double)ha.z + (double)la.z;
+        int cx, cy, cz;
+        cell_coords(S.nc, S.atom_cell[a], cx, cy, cz);
+        const float h = S.f_h;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = cx + dx, yy = cy + dy, zz = cz + dz;
+                    const bool inside = valid && xx >= 0 && yy >= 0 && zz >= 0 && xx < S.nc[0] &&
+                                        yy < S.nc[1] && zz < S.nc[2];
+                    if (inside) {
+                        const int cc = cell_rank(S.nc, xx, yy, zz);
+                        const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
+                        const unsigned code = nl_entry(0, dx, dy, dz);
+                        // position of atom a relative to the centre of cell cc
+                        const float ox = ra.x - (float)dx * h, oy = ra.y - (float)dy * h,
+                                    oz = ra.z - (float)dz * h;
+                        for (int j = s; j < e; ++j) {
+                            const float4 rj = S.rel[par][j];
+                            const float fx = rj.x - ox, fy = rj.y - oy, fz = rj.z - oz;
+                            const float r2f = fx * fx + fy * fy + fz * fz;
+                            bool in;
+                            if (r2f < S.f_rl2_lo)
+                                in = true;
+                            else if (r2f >= S.f_rl2_hi)
+                                in = false;
+                            else
+                                in = in_list(S, par, true, a, xa, ya, za, ha, la, j);
+                            if (in && j != a) {
+                                if (cnt < S.cap_use) wr.put(cnt, (int)(((unsigned)j << NL_CODE_BITS) | code));
+                                ++cnt;
+                            }
+                        }
+                    }
+                    wr.flush(min(__reduce_min_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 1 << 30),
+                                 wr.flushed + RW_ROWS));
+                }
+        const int top = __reduce_max_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 0);
+        wr.flush(top);
+        if (valid) {
+            S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
+            S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
+        }
+    } else if (u < S.ctl->nunits) {
         const bool mixed = S.prec != PTA_PREC_FP64;
         int a0, ga;
         unit_atoms(S, u, a0, ga);
@@ -396,6 +478,7 @@ void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_permute_gather<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_permute_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_unit_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_rel_all<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);
 }

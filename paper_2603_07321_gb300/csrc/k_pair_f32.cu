@@ -411,30 +411,35 @@ void launch_prune(const Tab &t, int force, cudaStream_t st) {
 void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st);
 void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st);
 
-#define PTA_LG_SWITCH(KER, ARG)                                                      \
+#define PTA_LAUNCH(KER, ...)                                                         \
+    do {                                                                             \
+        KER<__VA_ARGS__><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg);               \
+    } while (0)
+
+#define PTA_LG_SWITCH(KER)                                                           \
     if (g.G == 2) {                                                                  \
         switch (g.L) {                                                               \
-            case 1: KER<1, 2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
-            default: KER<2, 2, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            case 1: PTA_LAUNCH(KER, 1, 2, SC76); break;                              \
+            default: PTA_LAUNCH(KER, 2, 2, SC76); break;                             \
         }                                                                            \
     } else {                                                                         \
         switch (g.L) {                                                               \
-            case 1: KER<1, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
-            case 2: KER<2, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
-            case 4: KER<4, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
-            case 8: KER<8, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
-            default: KER<16, 1, SC76><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break; \
+            case 1: PTA_LAUNCH(KER, 1, 1, SC76); break;                              \
+            case 2: PTA_LAUNCH(KER, 2, 1, SC76); break;                              \
+            case 4: PTA_LAUNCH(KER, 4, 1, SC76); break;                              \
+            case 8: PTA_LAUNCH(KER, 8, 1, SC76); break;                              \
+            default: PTA_LAUNCH(KER, 16, 1, SC76); break;                            \
         }                                                                            \
     }
 
 template <bool SC76>
-static void density_f32(const Tab &t, const Group &g, int force, cudaStream_t st) {
-    PTA_LG_SWITCH(k_density_f32, force)
+static void density_f32(const Tab &t, const Group &g, int arg, cudaStream_t st) {
+    PTA_LG_SWITCH(k_density_f32)
 }
 
 template <bool SC76>
-static void force_f32(const Tab &t, const Group &g, int mode, cudaStream_t st) {
-    PTA_LG_SWITCH(k_force_f32, mode)
+static void force_f32(const Tab &t, const Group &g, int arg, cudaStream_t st) {
+    PTA_LG_SWITCH(k_force_f32)
 }
 
 void launch_density(const Tab &t, int force, cudaStream_t st) {

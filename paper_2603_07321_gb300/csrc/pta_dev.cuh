@@ -234,6 +234,32 @@ __device__ __forceinline__ void unit_atoms(const SpecDev &S, int u, int &a0, int
     }
 }
 
+// Rows of a warp's list tile (L = 1: row k holds entry k of the warp's 32
+// units) staged in shared memory and written to global memory as whole
+// 128-byte rows once every lane has passed them; a lane that runs more than
+// ROWS rows ahead of the flushed rows writes that entry and all its later
+// ones directly.
+template <int ROWS>
+struct RowWriter {
+    int *buf;   // shared [ROWS][32]
+    int *tile;  // global word of row 0 of this warp's tile
+    int lane, flushed, direct_from;
+    __device__ __forceinline__ void put(int k, int e) {
+        if (k < direct_from && k - flushed < ROWS) {
+            buf[(k % ROWS) * 32 + lane] = e;
+        } else {
+            tile[(long long)k * 32 + lane] = e;
+            direct_from = min(direct_from, k);
+        }
+    }
+    // warp-collective: write rows [flushed, upto)
+    __device__ __forceinline__ void flush(int upto) {
+        for (int r = flushed; r < upto; ++r)
+            if (r < direct_from) tile[(long long)r * 32 + lane] = buf[(r % ROWS) * 32 + lane];
+        flushed = upto;
+    }
+};
+
 // neighbour-list word of neighbour k of atom a for L lanes per atom: atoms
 // are grouped 32/L per warp; for each iteration q = k / L the warp's 32
 // words are contiguous, lane (a % (32/L)) * L + k % L.
