@@ -393,7 +393,7 @@ def run_pta(args, wl):
 
     # launches of this library's kernels in the timed region: per fine-step
     # iteration the decide kernel and, per (precision, lanes) group, the
-    # density and force passes; per list build 11 kernels; per pruning one
+    # density and force passes; per list build 12 kernels; per pruning one
     # kernel per group and one bookkeeping kernel; per burst the grip
     # increment, burst start and burst end; per coarse step the update
     groups = len({(c.params.precision, c.layout()["lanes"], c.layout()["atoms_per_thread"])
@@ -401,7 +401,7 @@ def run_pta(args, wl):
     builds = sum(b.rebuilds for step in results for r in step for b in r.burst)
     prunes = sum(b.prunes for step in results for r in step for b in r.burst)
     bursts = 3 * args.steps
-    launches = int(kt.iterations * (1 + 2 * groups) + builds * 11 + prunes * (groups + 1)
+    launches = int(kt.iterations * (1 + 2 * groups) + builds * 12 + prunes * (groups + 1)
                    + bursts * 3 + args.steps)
 
     # end to end through the public API with host buffers: per step the state

@@ -124,6 +124,14 @@ typedef struct {
                            prune_margin / 2 since the last pruning; it holds every
                            pair within rc in the same order, so results do not
                            change.  0 = default 0.3 A, < 0 = off               */
+    int cell_tiles;     /* mixed precision, one thread per atom: the pair passes
+                           take tiles of 2x2x2 cells per thread block and read
+                           the neighbours' records from a shared-memory copy of
+                           the 4x4x4 cells around the tile (per-atom results
+                           are unchanged).  1 = on (also makes the automatic
+                           lane count 1; PTA_EUNSUPPORTED for FP64,
+                           atoms_per_thread 2 or lanes > 1); 0 (default) and
+                           -1 = off                                          */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
@@ -198,6 +206,13 @@ int pta_natoms(const pta_ctx *ctx, int64_t *n);
  * (lanes), out[1] atoms per thread group, out[2] neighbour-list capacity per
  * atom, out[3] 1 when the pruned inner list is in use. */
 int pta_get_layout(const pta_ctx *ctx, int32_t out[4]);
+/* Cell tiles of this context (pta_params.cell_tiles): out[0] 1 when the pair
+ * passes use them, out[1] thread blocks of a pair pass (each takes every
+ * out[1]-th occupied tile), out[2] occupied tiles at the last list build,
+ * out[3] of those, tiles whose surrounding cells hold at most 3328 atoms and
+ * are read from the shared-memory copy (the others read global memory).
+ * Zeros after out[0] when tiles are off. */
+int pta_get_tiling(pta_ctx *ctx, int32_t out[4]);
 /* 0 mobile, 1 left grip, 2 right grip; n must equal the atom count */
 int pta_get_flags(pta_ctx *ctx, uint8_t *flags, int64_t n);
 

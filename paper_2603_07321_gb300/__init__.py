@@ -69,7 +69,7 @@ class Params(ctypes.Structure):
                 ("burst_steps", ctypes.c_int64), ("block_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("neigh_cap", ctypes.c_int),
                 ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
-                ("prune_margin", ctypes.c_double)]
+                ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int)]
 
 
 class Averages(ctypes.Structure):
@@ -120,6 +120,7 @@ _SIGS = {
     "pta_destroy": (None, [_VP]),
     "pta_natoms": (ctypes.c_int, [_VP, _P(ctypes.c_int64)]),
     "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
+    "pta_get_tiling": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_flags": (ctypes.c_int, [_VP, _P(ctypes.c_uint8), ctypes.c_int64]),
     "pta_apply_strain": (ctypes.c_int, [_VP, ctypes.c_double]),
     "pta_get_strain": (ctypes.c_int, [_VP, _P(ctypes.c_double)]),
@@ -277,6 +278,12 @@ def pta_get_layout(h) -> dict:
     _check(load().pta_get_layout(h, out), "pta_get_layout")
     return {"lanes": out[0], "atoms_per_thread": out[1], "neigh_cap": out[2],
             "pruned_list": bool(out[3])}
+
+
+def pta_get_tiling(h) -> dict:
+    out = (ctypes.c_int32 * 4)()
+    _check(load().pta_get_tiling(h, out), "pta_get_tiling")
+    return {"tiled": bool(out[0]), "blocks": out[1], "tiles": out[2], "staged_tiles": out[3]}
 
 
 def pta_get_flags(h, n):
@@ -469,6 +476,9 @@ class Ctx:
 
     def layout(self):
         return pta_get_layout(self.h)
+
+    def tiling(self):
+        return pta_get_tiling(self.h)
 
     def apply_strain(self, d_eps):
         pta_apply_strain(self.h, d_eps)

@@ -6,7 +6,7 @@
 // of edge >= rc + skin; atoms outside the grid are clamped onto its border
 // cells, which keeps every pair within reach (clamping is non-expansive).
 // After binning, the atoms themselves are permuted into cell order (cells in
-// increasing linear index, atoms of a cell in their previous order), so that
+// rank order, atoms of a cell in their previous order), so that
 // the 32 atoms of a warp share a cell and read overlapping neighbours, and a
 // cell's atoms are one contiguous range.  The list order (cell order, then
 // slot) is therefore a function of positions and grid: builds are
@@ -145,6 +145,91 @@ __global__ void k_scan(const SpecDev *__restrict__ specs, int force) {
     if (threadIdx.x == 0) {
         S.cell_start[S.ncell] = carry;
         S.ctl->rebuilds += 1;
+    }
+    if (!S.tiled) return;
+    // occupied tiles, in rank order (the cell starts above are visible to
+    // the whole block after the barrier)
+    __syncthreads();
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < S.ntile_grid; base += SCAN_THREADS) {
+        const int b = base + threadIdx.x;
+        const int v = (b < S.ntile_grid && S.cell_start[8 * b + 8] > S.cell_start[8 * b]) ? 1 : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
+        if (v) S.tile_list[excl] = b;
+        __syncthreads();
+        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) S.ctl->ntiles = carry;
+}
+
+// one warp per occupied tile: its atom range and the halo table (stage
+// offset and first slot of each of the 4x4x4 cells around it, cells outside
+// the grid empty); the halo is staged when it holds at most TILE_SC atoms
+__global__ void k_tile_table(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
+                             int force) {
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!S.tiled || !build_active(S, force)) return;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = S.nblk_atom * (TPB / 32);
+    const int nt = S.ctl->ntiles;
+    for (int k = (blockIdx.x - S.blk_atom0) * (TPB / 32) + (threadIdx.x >> 5); k < nt; k += nwarp) {
+        const int b = S.tile_list[k];
+        int bx, by, bz;
+        tile_coords(S.nc, b, bx, by, bz);
+        int cnt[2], st[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int hc = 2 * lane + i;
+            const int x = 2 * bx - 1 + (hc & 3), y = 2 * by - 1 + ((hc >> 2) & 3),
+                      z = 2 * bz - 1 + (hc >> 4);
+            cnt[i] = 0;
+            st[i] = 0;
+            if (x >= 0 && y >= 0 && z >= 0 && x < S.nc[0] && y < S.nc[1] && z < S.nc[2]) {
+                const int c = cell_rank(S.nc, x, y, z);
+                st[i] = S.cell_start[c];
+                cnt[i] = S.cell_start[c + 1] - st[i];
+            }
+        }
+        const int v = cnt[0] + cnt[1];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int excl = x - v;
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        int *T = S.tile_tab + (long long)b * TT_STRIDE;
+        T[TT_OFF + 2 * lane] = excl;
+        T[TT_OFF + 2 * lane + 1] = excl + cnt[0];
+        T[TT_START + 2 * lane] = st[0];
+        T[TT_START + 2 * lane + 1] = st[1];
+        if (lane == 0) {
+            T[TT_OFF + TILE_HALO] = total;
+            T[TT_A0] = S.cell_start[8 * b];
+            T[TT_A1] = S.cell_start[8 * b + 8];
+            T[TT_STAGED] = total <= TILE_SC ? 1 : 0;
+        }
     }
 }
 
@@ -310,15 +395,23 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         wr.lane = lane;
         wr.flushed = 0;
         wr.direct_from = 1 << 30;
-        for (int r = 0; r < RW_ROWS; ++r) wr.buf[r * 32 + lane] = (a << NL_CODE_BITS);  // valid filler
+        // filler rows hold entry 0: a valid index both of the atoms and of a
+        // staged halo
+        for (int r = 0; r < RW_ROWS; ++r) wr.buf[r * 32 + lane] = 0;
         __syncwarp();
         const float4 ra = S.rel[par][a];
         const float4 ha = ((const float4 *)S.pos[par])[a];
         const float4 la = S.lo[par][a];
         const double xa = (double)ha.x + (double)la.x, ya = (double)ha.y + (double)la.y,
                      za = (double)ha.z + (double)la.z;
+        const int ca = S.atom_cell[a];
         int cx, cy, cz;
-        cell_coords(S.nc, S.atom_cell[a], cx, cy, cz);
+        cell_coords(S.nc, ca, cx, cy, cz);
+        // tiled: entries of a staged tile index its halo copy; halo cell of
+        // the neighbour cell at offset d is (own cell in the tile + 1 + d)
+        const int *__restrict__ Tt = S.tiled ? S.tile_tab + (long long)(ca >> 3) * TT_STRIDE : nullptr;
+        const bool staged = Tt != nullptr && Tt[TT_STAGED] != 0;
+        const int hown = (1 + (ca & 1)) + 4 * (1 + ((ca >> 1) & 1)) + 16 * (1 + ((ca >> 2) & 1));
         const float h = S.f_h;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
@@ -330,6 +423,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                         const int cc = cell_rank(S.nc, xx, yy, zz);
                         const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
                         const unsigned code = nl_entry(0, dx, dy, dz);
+                        const int shift = staged ? Tt[TT_OFF + hown + dx + 4 * dy + 16 * dz] - s : 0;
                         // position of atom a relative to the centre of cell cc
                         const float ox = ra.x - (float)dx * h, oy = ra.y - (float)dy * h,
                                     oz = ra.z - (float)dz * h;
@@ -345,7 +439,8 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                             else
                                 in = in_list(S, par, true, a, xa, ya, za, ha, la, j);
                             if (in && j != a) {
-                                if (cnt < S.cap_use) wr.put(cnt, (int)(((unsigned)j << NL_CODE_BITS) | code));
+                                if (cnt < S.cap_use)
+                                    wr.put(cnt, (int)(((unsigned)(j + shift) << NL_CODE_BITS) | code));
                                 ++cnt;
                             }
                         }
@@ -356,6 +451,9 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         const int top = __reduce_max_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 0);
         wr.flush(top);
         if (valid) {
+            // the row after the last entry is read (and gathered) by the
+            // unrolled pair loops: a filler entry
+            wr.tile[(long long)min(cnt, S.cap_use) * 32 + lane] = 0;
             S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
             S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
         }
@@ -478,6 +576,7 @@ void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_permute_gather<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_permute_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_unit_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
+    k_tile_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_rel_all<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);

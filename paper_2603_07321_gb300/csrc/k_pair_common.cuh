@@ -28,22 +28,23 @@ __device__ __forceinline__ T lane_sum(T v) {
     return v;
 }
 
-// Called by every thread of a pair block after the warp reductions (values
-// valid in lane 0 of each warp).  Block partials go to S.part (8 doubles per
-// block); the last block of the specimen to finish sums all partials in a
-// fixed order and advances the specimen's control block:
+// Called by every thread of a pair block of NT threads after the warp
+// reductions (values valid in lane 0 of each warp); red is shared scratch of
+// 5 NT doubles.  Block partials go to S.part (8 doubles per block); the last
+// block of the specimen to finish sums all partials in a fixed order and
+// advances the specimen's control block:
 //   MODE_STEP, phase RUN:     sample (K, U, T) into the series, step count + 1,
 //                             burst over after nsteps samples
 //   MODE_STEP, phase REFRESH: forces refreshed and the first step started
 //   MODE_EVAL:                K, U, T stored in eval_obs
 // and in MODE_STEP the position buffers swap, the skin test sets the
 // rebuild flag and the pruning margin test the prune flag.
+template <int NT>
 __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double pe_w, double rr_w,
                                  double d2_w, double dp2_w, int mode, int phase, long long done,
-                                 long long nsteps) {
+                                 long long nsteps, double (*red)[NT]) {
     constexpr int NV = 5;  // K, U, R, max displacement^2 since the build and since the pruning
-    __shared__ double shw[NV][TPB / 32];
-    __shared__ double red[NV][TPB];
+    __shared__ double shw[NV][NT / 32];
     __shared__ int is_last;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -56,7 +57,7 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
     __syncthreads();
     if (threadIdx.x == 0) {
         double k = 0, p = 0, r = 0, d = 0, e = 0;
-        for (int i = 0; i < TPB / 32; ++i) {
+        for (int i = 0; i < NT / 32; ++i) {
             k = k + shw[0][i];
             p = p + shw[1][i];
             r = r + shw[2][i];
@@ -77,7 +78,7 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
     if (!is_last) return;
     __threadfence();
     double v[NV] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < S.nblk_pair; b += TPB) {
+    for (int b = threadIdx.x; b < S.nblk_pair; b += NT) {
         const double *P = S.part + 8LL * b;
         v[0] = v[0] + __ldcg(P);
         v[1] = v[1] + __ldcg(P + 1);
@@ -87,7 +88,21 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
     }
     for (int q = 0; q < NV; ++q) red[q][threadIdx.x] = v[q];
     __syncthreads();
-    for (int s = TPB / 2; s > 0; s >>= 1) {
+    // pairwise tree over the largest power of two P <= NT, after folding the
+    // NT - P top entries onto the first ones
+    constexpr int P = (NT & (NT - 1)) == 0 ? NT : (NT >= 256 && NT < 512 ? 256 : 0);
+    static_assert(P > 0, "block size");
+    if (P < NT) {
+        if (threadIdx.x < NT - P) {
+            red[0][threadIdx.x] = red[0][threadIdx.x] + red[0][threadIdx.x + P];
+            red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + P];
+            red[2][threadIdx.x] = red[2][threadIdx.x] + red[2][threadIdx.x + P];
+            red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + P]);
+            red[4][threadIdx.x] = fmax(red[4][threadIdx.x], red[4][threadIdx.x + P]);
+        }
+        __syncthreads();
+    }
+    for (int s = P / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
             red[0][threadIdx.x] = red[0][threadIdx.x] + red[0][threadIdx.x + s];
             red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + s];

@@ -125,6 +125,80 @@ struct ForceAcc {
     }
 };
 
+// After the force pass of atom a (force f, energy sum en, F'(rho_a) = fpa):
+// its energy, its share of the reaction, and the velocity-Verlet update --
+// the half-kick that finishes the step (phase RUN), the sample of K, and
+// unless the burst ends the half-kick and drift of the next step; the new
+// position (hi + lo, whole grid quanta moved from lo to hi), its record
+// relative to its cell centre, and the displacements since the last list
+// build and pruning.  Grip atoms keep v = 0.  MODE_EVAL stores F and the
+// energy instead.
+__device__ __forceinline__ void atom_update(const SpecDev &S, SpecCtl *ctl, int par, int a,
+                                            float fpa, float fx, float fy, float fz, float en,
+                                            int mode, int phase, long long done, long long nsteps,
+                                            float &ke, float &pe, float &rr, float &d2, float &dp2) {
+    const float eps = S.pot.f_eps;
+    const float pe_a = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
+    pe += pe_a;
+    const uint8_t flag = S.flags[a];
+    if (flag == FLAG_RIGHT) rr -= (S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
+    float4 v = ((const float4 *)S.vel)[a];
+    if (mode == MODE_EVAL) {
+        ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+        double4_32a *o = (double4_32a *)S.eval_out;
+        o[S.orig[a]] = make_double4_32a(fx, fy, fz, pe_a);
+        return;
+    }
+    const float kh = S.f_acc_half;
+    if (phase == PH_RUN) {
+        if (flag == FLAG_MOBILE) {
+            v.x += fx * kh;
+            v.y += fy * kh;
+            v.z += fz * kh;
+        }
+        ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+    const float4 hia = ((const float4 *)S.pos[par])[a];
+    const float4 loa = S.lo[par][a];
+    float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
+    const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
+    if (start && flag == FLAG_MOBILE) {
+        v.x += fx * kh;
+        v.y += fy * kh;
+        v.z += fz * kh;
+        const float dt = S.f_dt;
+        qq[0] += v.x * dt;
+        qq[1] += v.y * dt;
+        qq[2] += v.z * dt;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            // move whole grid quanta from lo to hi (both steps exact)
+            const float sh = rintf(qq[d] * (float)HI_SCALE) * (float)HI_QUANTUM;
+            hh[d] = hh[d] + sh;
+            qq[d] = qq[d] - sh;
+        }
+        if (fabsf(hh[0]) > (float)MIXED_RANGE || fabsf(hh[1]) > (float)MIXED_RANGE ||
+            fabsf(hh[2]) > (float)MIXED_RANGE)
+            atomicOr(&ctl->err, ERR_RANGE);
+    }
+    ((float4 *)S.pos[par ^ 1])[a] = make_float4(hh[0], hh[1], hh[2], 0.f);
+    S.lo[par ^ 1][a] = make_float4(qq[0], qq[1], qq[2], 0.f);
+    const float3 C = cell_centre(S, S.atom_cell[a]);
+    S.rel[par ^ 1][a] = make_float4((hh[0] - C.x) + qq[0], (hh[1] - C.y) + qq[1],
+                                    (hh[2] - C.z) + qq[2], 0.f);
+    ((float4 *)S.vel)[a] = v;
+    const float4 rf = S.ref[a];
+    const float ex = (hh[0] - rf.x) + qq[0], ey = (hh[1] - rf.y) + qq[1],
+                ez = (hh[2] - rf.z) + qq[2];
+    d2 = fmaxf(d2, ex * ex + ey * ey + ez * ez);
+    if (S.prune_on) {
+        const float4 pf = S.pref[a];
+        const float px = (hh[0] - pf.x) + qq[0], py = (hh[1] - pf.y) + qq[1],
+                    pz = (hh[2] - pf.z) + qq[2];
+        dp2 = fmaxf(dp2, px * px + py * py + pz * pz);
+    }
+}
+
 template <int L, int G, bool SC76>
 __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restrict__ specs,
                                                         const int *__restrict__ b2s, int force) {
@@ -234,74 +308,13 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
         acc.fz[g] = lane_sum<L>(acc.fz[g]);
         acc.en[g] = lane_sum<L>(acc.en[g]);
     }
-    const float eps = S.pot.f_eps;
     float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f, dp2 = 0.f;
     if (valid && l == 0) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const int a = a0 + g;
             if (g >= ga) continue;
-            const float fx = acc.fx[g], fy = acc.fy[g], fz = acc.fz[g];
-            const float fpa = ra[g].w;
-            const float pe_a = 0.5f * eps * acc.en[g] + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
-            pe += pe_a;
-            const uint8_t flag = S.flags[a];
-            if (flag == FLAG_RIGHT) rr -= (S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));
-            float4 v = ((const float4 *)S.vel)[a];
-            if (mode == MODE_EVAL) {
-                ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
-                double4_32a *o = (double4_32a *)S.eval_out;
-                o[S.orig[a]] = make_double4_32a(fx, fy, fz, pe_a);
-                continue;
-            }
-            const float kh = S.f_acc_half;
-            if (phase == PH_RUN) {
-                if (flag == FLAG_MOBILE) {
-                    v.x += fx * kh;
-                    v.y += fy * kh;
-                    v.z += fz * kh;
-                }
-                ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
-            }
-            const float4 hia = ((const float4 *)S.pos[par])[a];
-            const float4 loa = S.lo[par][a];
-            float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
-            const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
-            if (start && flag == FLAG_MOBILE) {
-                v.x += fx * kh;
-                v.y += fy * kh;
-                v.z += fz * kh;
-                const float dt = S.f_dt;
-                qq[0] += v.x * dt;
-                qq[1] += v.y * dt;
-                qq[2] += v.z * dt;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    // move whole grid quanta from lo to hi (both steps exact)
-                    const float sh = rintf(qq[d] * (float)HI_SCALE) * (float)HI_QUANTUM;
-                    hh[d] = hh[d] + sh;
-                    qq[d] = qq[d] - sh;
-                }
-                if (fabsf(hh[0]) > (float)MIXED_RANGE || fabsf(hh[1]) > (float)MIXED_RANGE ||
-                    fabsf(hh[2]) > (float)MIXED_RANGE)
-                    atomicOr(&ctl->err, ERR_RANGE);
-            }
-            ((float4 *)S.pos[par ^ 1])[a] = make_float4(hh[0], hh[1], hh[2], 0.f);
-            S.lo[par ^ 1][a] = make_float4(qq[0], qq[1], qq[2], 0.f);
-            const float3 C = cell_centre(S, S.atom_cell[a]);
-            S.rel[par ^ 1][a] = make_float4((hh[0] - C.x) + qq[0], (hh[1] - C.y) + qq[1],
-                                            (hh[2] - C.z) + qq[2], 0.f);
-            ((float4 *)S.vel)[a] = v;
-            const float4 rf = S.ref[a];
-            const float ex = (hh[0] - rf.x) + qq[0], ey = (hh[1] - rf.y) + qq[1],
-                        ez = (hh[2] - rf.z) + qq[2];
-            d2 = fmaxf(d2, ex * ex + ey * ey + ez * ez);
-            if (S.prune_on) {
-                const float4 pf = S.pref[a];
-                const float px = (hh[0] - pf.x) + qq[0], py = (hh[1] - pf.y) + qq[1],
-                            pz = (hh[2] - pf.z) + qq[2];
-                dp2 = fmaxf(dp2, px * px + py * py + pz * pz);
-            }
+            atom_update(S, ctl, par, a0 + g, ra[g].w, acc.fx[g], acc.fy[g], acc.fz[g], acc.en[g],
+                        mode, phase, done, nsteps, ke, pe, rr, d2, dp2);
         }
     }
     ke = warp_sum(ke);
@@ -309,8 +322,9 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
     rr = warp_sum(rr);
     d2 = warp_max(d2);
     dp2 = warp_max(dp2);
-    step_tail(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode, phase, done,
-              nsteps);
+    __shared__ double red[5][TPB];
+    step_tail<TPB>(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode, phase,
+                   done, nsteps, red);
 }
 
 // Inner list: every lane keeps, in order, the entries of its own column of
@@ -383,11 +397,227 @@ __global__ void k_prune_done(const SpecDev *__restrict__ specs, int force) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cell tiles (mixed precision, one lane per atom)
+// ---------------------------------------------------------------------------
+// Block k of a specimen takes the occupied tiles k, k + nblk_pair, ... in
+// turn.  For a staged tile the 16-byte records of the atoms of the 4x4x4
+// cells around it are first copied into shared memory (cell by cell, one
+// warp per cell), and its list entries are indices into that copy; the
+// per-neighbour gathers are then shared-memory loads.  The tile's atoms are
+// one contiguous range, one thread per atom.  Each atom sums its list in
+// the same order and with the same arithmetic as the one-lane kernels above,
+// so the per-atom results are identical; only the grouping of the per-block
+// partials of K, U and R differs.
+
+__device__ __forceinline__ void tile_stage(const int *__restrict__ T, const float4 *__restrict__ src,
+                                           float4 *stg) {
+    const int lane = threadIdx.x & 31;
+    for (int hc = threadIdx.x >> 5; hc < TILE_HALO; hc += TILE_T / 32) {
+        const int o = T[TT_OFF + hc], cnt = T[TT_OFF + hc + 1] - o, g = T[TT_START + hc];
+        for (int i = lane; i < cnt; i += 32) stg[o + i] = __ldg(src + g + i);
+    }
+}
+
+template <bool ST>
+__device__ __forceinline__ float4 tile_rec(const float4 *__restrict__ glob, const float4 *stg,
+                                           unsigned e) {
+    if (ST) return stg[nl_j(e)];
+    return __ldg(glob + nl_j(e));
+}
+
+template <bool SC76, bool ST>
+__device__ __forceinline__ float tile_rho(const SpecDev &S, const float4 *__restrict__ rel,
+                                          const float4 *stg, const unsigned *__restrict__ lst,
+                                          int cl, float4 r0) {
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float3 dg0 = make_float3(0.f, 0.f, 0.f);
+    DensityAcc<1, SC76> acc;
+    acc.rho[0] = 0.f;
+    unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
+    for (int q = 0; q < cl; q += 2) {
+        const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+        const float4 xa = tile_rec<ST>(rel, stg, ea);
+        const float4 xb = tile_rec<ST>(rel, stg, eb);
+        acc.add(S, entry_disp(ea, xa, r0, h, h8, h64), &dg0, 1);
+        if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, r0, h, h8, h64), &dg0, 1);
+        ea = na;
+        eb = nb;
+    }
+    return acc.rho[0];
+}
+
+template <bool SC76, bool ST>
+__device__ __forceinline__ void tile_force(const SpecDev &S, const float4 *__restrict__ lf,
+                                           const float4 *stg, const unsigned *__restrict__ lst,
+                                           int cl, float4 r0, ForceAcc<1, SC76> &acc) {
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float3 dg0 = make_float3(0.f, 0.f, 0.f);
+    unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
+    for (int q = 0; q < cl; q += 2) {
+        const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+        const float4 xa = tile_rec<ST>(lf, stg, ea);
+        const float4 xb = tile_rec<ST>(lf, stg, eb);
+        acc.add(S, entry_disp(ea, xa, r0, h, h8, h64), xa.w, &dg0, &r0, 1);
+        if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, r0, h, h8, h64), xb.w, &dg0, &r0, 1);
+        ea = na;
+        eb = nb;
+    }
+}
+
+template <bool SC76>
+__global__ void __launch_bounds__(TILE_T, 4) k_density_tile(const SpecDev *__restrict__ specs,
+                                                            const int *__restrict__ b2s, int force) {
+    extern __shared__ float4 stg[];
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    const SpecCtl *ctl = S.ctl;
+    if (!force && ctl->phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    const float4 *__restrict__ rel = S.rel[par];
+    const int nt = ctl->ntiles;
+    for (int k = blockIdx.x - S.blk_pair0; k < nt; k += S.nblk_pair) {
+        const int *__restrict__ T = S.tile_tab + (long long)__ldg(S.tile_list + k) * TT_STRIDE;
+        const int a0 = __ldg(T + TT_A0), a1 = __ldg(T + TT_A1);
+        const bool st = __ldg(T + TT_STAGED) != 0;
+        if (st) {
+            __syncthreads();
+            tile_stage(T, rel, stg);
+            __syncthreads();
+        }
+        for (int a = a0 + threadIdx.x; a < a1; a += TILE_T) {
+            int cl;
+            const unsigned *__restrict__ lst = lane_list(S, a, 0, 1, cl);
+            const float4 r0 = rel[a];
+            const float rho = st ? tile_rho<SC76, true>(S, rel, stg, lst, cl, r0)
+                                 : tile_rho<SC76, false>(S, rel, stg, lst, cl, r0);
+            const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
+            ((float4 *)S.posfp)[a] = make_float4(r0.x, r0.y, r0.z, fp);
+        }
+    }
+}
+
+template <bool SC76>
+__global__ void __launch_bounds__(TILE_T, 3) k_force_tile(const SpecDev *__restrict__ specs,
+                                                          const int *__restrict__ b2s, int mode) {
+    extern __shared__ float4 stg[];
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    SpecCtl *ctl = S.ctl;
+    const int phase = ctl->phase;
+    if (mode == MODE_STEP && phase == PH_IDLE) return;
+    const int par = ctl->parity;
+    const long long done = ctl->done, nsteps = ctl->nsteps;
+    const int lb = blockIdx.x - S.blk_pair0;
+    const float4 *__restrict__ lf = (const float4 *)S.posfp;
+    const int nt = ctl->ntiles;
+    float ke = 0.f, pe = 0.f, rr = 0.f, d2 = 0.f, dp2 = 0.f;
+    for (int k = lb; k < nt; k += S.nblk_pair) {
+        const int *__restrict__ T = S.tile_tab + (long long)__ldg(S.tile_list + k) * TT_STRIDE;
+        const int a0 = __ldg(T + TT_A0), a1 = __ldg(T + TT_A1);
+        const bool st = __ldg(T + TT_STAGED) != 0;
+        if (st) {
+            __syncthreads();
+            tile_stage(T, lf, stg);
+            __syncthreads();
+        }
+        for (int a = a0 + threadIdx.x; a < a1; a += TILE_T) {
+            int cl;
+            const unsigned *__restrict__ lst = lane_list(S, a, 0, 1, cl);
+            const float4 r0 = lf[a];
+            ForceAcc<1, SC76> acc;
+            acc.fx[0] = acc.fy[0] = acc.fz[0] = acc.en[0] = 0.f;
+            if (st)
+                tile_force<SC76, true>(S, lf, stg, lst, cl, r0, acc);
+            else
+                tile_force<SC76, false>(S, lf, stg, lst, cl, r0, acc);
+            atom_update(S, ctl, par, a, r0.w, acc.fx[0], acc.fy[0], acc.fz[0], acc.en[0], mode,
+                        phase, done, nsteps, ke, pe, rr, d2, dp2);
+        }
+    }
+    ke = warp_sum(ke);
+    pe = warp_sum(pe);
+    rr = warp_sum(rr);
+    d2 = warp_max(d2);
+    dp2 = warp_max(dp2);
+    __syncthreads();  // the stage is reused as reduction scratch
+    step_tail<TILE_T>(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode,
+                      phase, done, nsteps, reinterpret_cast<double (*)[TILE_T]>(stg));
+}
+
+// pruning of a tile's lists: the same test and order as k_prune_f32<1, 1>,
+// with staged records; the row after the last kept entry gets a filler
+__global__ void __launch_bounds__(TILE_T, 3) k_prune_tile(const SpecDev *__restrict__ specs,
+                                                          const int *__restrict__ b2s, int force) {
+    extern __shared__ float4 stg[];
+    const SpecDev &S = specs[b2s[blockIdx.x]];
+    if (!prune_active(S, force)) return;
+    const SpecCtl *ctl = S.ctl;
+    const int par = ctl->parity;
+    const float4 *__restrict__ rel = S.rel[par];
+    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64, rp2 = S.f_rp2;
+    const int nt = ctl->ntiles;
+    for (int k = blockIdx.x - S.blk_pair0; k < nt; k += S.nblk_pair) {
+        const int *__restrict__ T = S.tile_tab + (long long)__ldg(S.tile_list + k) * TT_STRIDE;
+        const int a0 = __ldg(T + TT_A0), a1 = __ldg(T + TT_A1);
+        const bool st = __ldg(T + TT_STAGED) != 0;
+        if (st) {
+            __syncthreads();
+            tile_stage(T, rel, stg);
+            __syncthreads();
+        }
+        for (int a = a0 + threadIdx.x; a < a1; a += TILE_T) {
+            const float4 r0 = rel[a];
+            const long long off = nl_base(a, 1, S.cap);
+            const unsigned *__restrict__ src = (const unsigned *)S.nlist + off;
+            unsigned *__restrict__ dst = (unsigned *)S.plist + off;
+            const int nn = S.nn[a];
+            int kept = 0;
+            for (int q = 0; q < nn; ++q) {
+                const unsigned e = __ldg(src + q * 32);
+                const float4 x = st ? tile_rec<true>(rel, stg, e) : tile_rec<false>(rel, stg, e);
+                const float3 d = entry_disp(e, x, r0, h, h8, h64);
+                const float ex = d.x - 0.f, ey = d.y - 0.f, ez = d.z - 0.f;
+                if (ex * ex + ey * ey + ez * ez < rp2) dst[(kept++) * 32] = e;
+            }
+            dst[kept * 32] = 0u;
+            S.pnn[a] = kept;
+            const float4 hi = ((const float4 *)S.pos[par])[a];
+            const float4 lo = S.lo[par][a];
+            S.pref[a] = make_float4(hi.x + lo.x, hi.y + lo.y, hi.z + lo.z, 0.f);
+        }
+    }
+}
+
+static constexpr size_t TILE_SMEM = (size_t)TILE_SC * sizeof(float4);
+static_assert(TILE_SMEM >= 5 * TILE_T * sizeof(double), "stage too small for the reduction");
+
+// opt the tile kernels into the dynamic shared memory they use (once)
+int tile_kernels_init() {
+    static int rc = -1;
+    if (rc >= 0) return rc;
+    const int b = (int)TILE_SMEM;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_density_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_density_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_force_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_force_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prune_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    rc = (e == cudaSuccess) ? 0 : 1;
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
 void launch_prune(const Tab &t, int force, cudaStream_t st) {
     for (int i = 0; i < t.ngroups; ++i) {
         const Group &g = t.grp[i];
         if (g.nblk <= 0 || g.prec == PTA_PREC_FP64) continue;
-        if (g.G == 2) {
+        if (g.tiled) {
+            k_prune_tile<<<g.nblk, TILE_T, TILE_SMEM, st>>>(t.specs, g.b2s, force);
+        } else if (g.G == 2) {
             if (g.L == 1)
                 k_prune_f32<1, 2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force);
             else
@@ -448,6 +678,10 @@ void launch_density(const Tab &t, int force, cudaStream_t st) {
         if (g.nblk <= 0) continue;
         if (g.prec == PTA_PREC_FP64)
             launch_density_f64(t, g, force, st);
+        else if (g.tiled && g.sc76)
+            k_density_tile<true><<<g.nblk, TILE_T, TILE_SMEM, st>>>(t.specs, g.b2s, force);
+        else if (g.tiled)
+            k_density_tile<false><<<g.nblk, TILE_T, TILE_SMEM, st>>>(t.specs, g.b2s, force);
         else if (g.sc76)
             density_f32<true>(t, g, force, st);
         else
@@ -461,6 +695,10 @@ void launch_force(const Tab &t, int mode, cudaStream_t st) {
         if (g.nblk <= 0) continue;
         if (g.prec == PTA_PREC_FP64)
             launch_force_f64(t, g, mode, st);
+        else if (g.tiled && g.sc76)
+            k_force_tile<true><<<g.nblk, TILE_T, TILE_SMEM, st>>>(t.specs, g.b2s, mode);
+        else if (g.tiled)
+            k_force_tile<false><<<g.nblk, TILE_T, TILE_SMEM, st>>>(t.specs, g.b2s, mode);
         else if (g.sc76)
             force_f32<true>(t, g, mode, st);
         else

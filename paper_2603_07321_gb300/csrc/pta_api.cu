@@ -248,7 +248,7 @@ static PotDev make_pot(const pta_potential &p) {
 struct Sizes {
     long long n, nunits;
     int L, G, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
-    int prune_on;
+    int prune_on, tiled, ntile_grid;
     double prune_margin;
     double h, org[3];
     size_t list_words;
@@ -272,13 +272,20 @@ static int valid_lanes(int L) { return L == 1 || L == 2 || L == 4 || L == 8 || L
 static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pta_params &par,
                          Sizes *z) {
     z->n = 4LL * s.n_cells[0] * s.n_cells[1] * s.n_cells[2];
-    z->L = par.lanes ? par.lanes : auto_lanes(z->n, par.precision);
+    z->L = par.lanes ? par.lanes
+                     : (par.cell_tiles == 1 ? 1 : auto_lanes(z->n, par.precision));
     // atoms per thread group: 1 unless asked for 2 (two atoms of one cell
     // sharing a union list read each neighbour record once for both, but the
     // two per-atom branches per entry cost more issue slots than the saved
     // reads on GB300, measured on the 470,596-atom cube)
     z->G = par.atoms_per_thread ? par.atoms_per_thread : 1;
     z->nunits = z->n;  // capacity; G = 2 sets the exact count at every build (below)
+    // cell tiles only on request: on GB300 their shared-memory gathers take
+    // as many L1 wavefronts as the global gathers they replace (8-9 per warp
+    // request from bank conflicts), and the 384-thread tile blocks run at
+    // lower occupancy, so they measured slower on the 470,596-atom cube
+    z->tiled = (par.precision == PTA_PREC_MIXED && z->G == 1 && z->L == 1 && par.cell_tiles == 1)
+                   ? 1 : 0;
     const double rl = p.rc + par.skin;
     z->prune_margin = par.prune_margin == 0.0 ? 0.3 : par.prune_margin;
     z->prune_on = (par.precision == PTA_PREC_MIXED && z->prune_margin > 0.0 &&
@@ -312,14 +319,28 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     for (int d = 0; d < 3; ++d) {
         z->org[d] = std::floor(-margin * 4096.0) / 4096.0;
         z->nc[d] = (int)std::floor((span[d] + 2.0 * margin) / z->h) + 1;
+        z->nc[d] += z->nc[d] & 1;  // whole tiles of 2x2x2 cells
         ncell *= z->nc[d];
     }
     if (ncell > (1LL << 30)) return PTA_EINVAL;
     z->ncell = (int)ncell;
+    z->ntile_grid = (int)(ncell / 8);
     z->nblk_cell = (z->ncell + CELL_WARPS - 1) / CELL_WARPS;
     // G = 2: at most one one-atom unit per cell besides the pairs
     if (z->G == 2) z->nunits = std::min<long long>(z->n, (z->n + 1) / 2 + z->ncell);
     z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
+    if (z->tiled) {
+        // one block per tile the specimen can occupy: an extent E meets at
+        // most floor(E / 2h) + 2 tiles per axis (10% more extent along the
+        // load axis for the strain); blocks loop when more tiles are occupied
+        long long nb = 1;
+        for (int d = 0; d < 3; ++d) {
+            const double ext = span[d] * (d == s.load_axis ? 1.1 : 1.0);
+            long long k = (long long)std::floor(ext / (2.0 * z->h)) + 2;
+            nb *= std::min<long long>(k, z->nc[d] / 2);
+        }
+        z->nblk_pair = (int)nb;
+    }
     const long long W = 32 / z->L;
     z->list_words = (size_t)((z->nunits + W - 1) / W) * W * z->cap;
     z->series_cap = std::max<long long>(par.burst_steps, 1);
@@ -357,6 +378,10 @@ static size_t footprint(const Sizes &z, int prec) {
         add(16 * n);                 // pref
     }
     add(4 * (size_t)z.nunits);       // nn
+    if (z.tiled) {
+        add(4 * (size_t)z.ntile_grid);             // tile_list
+        add(4 * (size_t)z.ntile_grid * TT_STRIDE); // tile_tab
+    }
     if (z.G == 2) {
         add(4 * n);                  // unit_first
         add(4 * ((size_t)z.ncell + 1));  // unit_cell
@@ -390,6 +415,10 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
         (par->precision == PTA_PREC_FP64 || (par->lanes != 0 && par->lanes > 2)))
         return PTA_EUNSUPPORTED;
     if (par->neigh_cap < 0 || par->neigh_cap > 4096) return PTA_EINVAL;
+    if (par->cell_tiles < -1 || par->cell_tiles > 1) return PTA_EINVAL;
+    if (par->cell_tiles == 1 && (par->precision == PTA_PREC_FP64 || par->atoms_per_thread == 2 ||
+                                 (par->lanes != 0 && par->lanes != 1)))
+        return PTA_EUNSUPPORTED;
     if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
     if (n > (long long)MAX_ATOMS) return PTA_ERANGE;
@@ -544,7 +573,7 @@ static int runner_upload(Runner *r) {
     int blk_atom = 0, blk_cell = 0;
     std::vector<int> b2s_atom, b2s_cell;
     struct Key {
-        int prec, L, G, sc76;
+        int prec, L, G, sc76, tiled;
     };
     std::vector<Key> keys;
     std::vector<std::vector<int>> gb2s;
@@ -560,11 +589,11 @@ static int runner_upload(Runner *r) {
         int g = -1;
         for (size_t q = 0; q < keys.size(); ++q)
             if (keys[q].prec == s.prec && keys[q].L == s.L && keys[q].G == s.G &&
-                keys[q].sc76 == s.pot.sc76)
+                keys[q].sc76 == s.pot.sc76 && keys[q].tiled == s.tiled)
                 g = (int)q;
         if (g < 0) {
             if (keys.size() >= 8) return PTA_EUNSUPPORTED;
-            keys.push_back({s.prec, s.L, s.G, s.pot.sc76});
+            keys.push_back({s.prec, s.L, s.G, s.pot.sc76, s.tiled});
             gb2s.emplace_back();
             g = (int)keys.size() - 1;
         }
@@ -622,6 +651,7 @@ static int runner_upload(Runner *r) {
         t.grp[q].L = keys[q].L;
         t.grp[q].G = keys[q].G;
         t.grp[q].sc76 = keys[q].sc76;
+        t.grp[q].tiled = keys[q].tiled;
         t.grp[q].b2s = tabs + off;
         t.grp[q].nblk = (int)gb2s[q].size();
         off += gb2s[q].size();
@@ -903,6 +933,7 @@ int pta_default_params(pta_params *p) {
     p->precision = PTA_PREC_FP64;
     p->neigh_cap = 0;
     p->lanes = 0;
+    p->cell_tiles = 0;
     return PTA_OK;
 }
 
@@ -963,6 +994,10 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
         AL(pref, 16 * n, float4 *);
     }
     AL(nn, 4 * (size_t)z.nunits, int *);
+    if (z.tiled) {
+        AL(tile_list, 4 * (size_t)z.ntile_grid, int *);
+        AL(tile_tab, 4 * (size_t)z.ntile_grid * TT_STRIDE, int *);
+    }
     if (z.G == 2) {
         AL(unit_first, 4 * n, int *);
         AL(unit_cell, 4 * ((size_t)z.ncell + 1), int *);
@@ -1000,6 +1035,7 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     }
     Sizes z;
     rc = compute_sizes(c->spec, c->pot, c->par, &z);
+    if (rc == PTA_OK && z.tiled && tile_kernels_init() != 0) rc = PTA_ECUDA;
     if (rc != PTA_OK) {
         delete c;
         return rc;
@@ -1017,6 +1053,8 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.nblk_pair = z.nblk_pair;
     s.nblk_atom = z.nblk_atom;
     s.nblk_cell = z.nblk_cell;
+    s.tiled = z.tiled;
+    s.ntile_grid = z.ntile_grid;
     for (int d = 0; d < 3; ++d) {
         s.ncl[d] = c->spec.n_cells[d];
         s.org[d] = z.org[d];
@@ -1123,6 +1161,27 @@ int pta_get_layout(const pta_ctx *c, int32_t out[4]) {
     out[1] = c->hd.G;
     out[2] = c->hd.cap_use;
     out[3] = c->hd.prune_on;
+    return PTA_OK;
+}
+
+int pta_get_tiling(pta_ctx *c, int32_t out[4]) {
+    if (!c || !out) return PTA_EINVAL;
+    for (int q = 0; q < 4; ++q) out[q] = 0;
+    out[0] = c->hd.tiled;
+    if (!c->hd.tiled) return PTA_OK;
+    if (c->broken) return PTA_ECUDA;
+    out[1] = c->hd.nblk_pair;
+    SpecCtl ctl;
+    std::vector<int> tab((size_t)c->hd.ntile_grid * TT_STRIDE), list((size_t)c->hd.ntile_grid);
+    CK(cudaMemcpyAsync(&ctl, c->hd.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(tab.data(), c->hd.tile_tab, 4 * tab.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(list.data(), c->hd.tile_list, 4 * list.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out[2] = ctl.ntiles;
+    for (int k = 0; k < ctl.ntiles && k < (int)list.size(); ++k)
+        out[3] += tab[(size_t)list[k] * TT_STRIDE + TT_STAGED] != 0;
     return PTA_OK;
 }
 
@@ -1288,6 +1347,15 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     CK(cudaStreamSynchronize(c->stream));
     *max_count = ctl.max_nn;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
+    // tiled: entries of a staged tile are slots of its halo copy; map them
+    // back through the tile table (stage offset and first slot of each halo cell)
+    std::vector<int> ttab, acell;
+    if (s.tiled) {
+        ttab.resize((size_t)s.ntile_grid * TT_STRIDE);
+        acell.resize((size_t)n);
+        CK(cudaMemcpy(ttab.data(), s.tile_tab, 4 * ttab.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(acell.data(), s.atom_cell, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+    }
     std::vector<int> ufirst;
     if (s.G == 2) {
         ufirst.resize((size_t)ctl.nunits);
@@ -1304,8 +1372,16 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
         for (int g = 0; g < ga; ++g) {
             const int64_t a = a0 + g;
             row.clear();
+            const int *T = s.tiled ? &ttab[(size_t)(acell[a] >> 3) * TT_STRIDE] : nullptr;
             for (int k = 0; k < nn[u]; ++k) {
-                const int j = nl_j((unsigned)raw[(size_t)nl_index((int)u, k, s.L, s.cap)]);
+                int j = nl_j((unsigned)raw[(size_t)nl_index((int)u, k, s.L, s.cap)]);
+                if (T && T[TT_STAGED]) {
+                    const int *off = T + TT_OFF;
+                    const int hc = (int)(std::upper_bound(off, off + TILE_HALO + 1, j) - off) - 1;
+                    if (hc < 0 || hc >= TILE_HALO || j >= off[TILE_HALO]) return PTA_ECUDA;
+                    j = T[TT_START + hc] + (j - off[hc]);
+                }
+                if (j < 0 || j >= n) return PTA_ECUDA;
                 if (s.G > 1) {
                     // the same FP64 predicate as the list build (no contraction)
                     if (j == a) continue;

@@ -19,6 +19,20 @@ constexpr int TPB = 128;        // threads per block of the atom and pair kernel
 constexpr int CELL_WARPS = 8;   // warps per block of the cell-sort kernel
 constexpr int SCAN_THREADS = 1024;
 
+// Cell tiles of the mixed-precision, one-lane-per-atom pair passes: a block
+// takes a tile of 2x2x2 cells; every neighbour of its atoms lies in the
+// 4x4x4 cells around it (the tile's halo, cells numbered hx + 4 hy + 16 hz).
+// When the halo holds at most TILE_SC atoms their records are copied into
+// shared memory and the tile's list entries index that copy.
+constexpr int TILE_T = 384;      // threads per block of the tile kernels
+constexpr int TILE_SC = 3328;    // records a staged halo may hold (52 KB)
+constexpr int TILE_HALO = 64;
+// per-tile table (ints): first atom, end atom, staged flag, stage offset of
+// each halo cell (65 entries, the last = halo atoms), first slot of each
+// halo cell (64)
+constexpr int TT_A0 = 0, TT_A1 = 1, TT_STAGED = 2, TT_OFF = 3, TT_START = TT_OFF + TILE_HALO + 1;
+constexpr int TT_STRIDE = TT_START + TILE_HALO;  // 132
+
 // grid quantum of the mixed-precision position split x = hi + lo:
 // hi is a multiple of 2^-12 A (exact in FP32 for |x| < 512 A), |lo| <= 2^-13 A
 constexpr double HI_SCALE = 4096.0;
@@ -61,6 +75,7 @@ struct SpecCtl {
     int nunits;                // units in use (G = 2: pairs of atoms of one cell)
     int prune;                 // 1: prune the inner list before the next pair pass
     int prunes;                // prunings in the current burst
+    int ntiles;                // occupied cell tiles at the last build
     double sum[3];             // running sums of K, U, T over the burst
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
@@ -78,6 +93,8 @@ struct SpecDev {
     int blk_atom0, nblk_atom;  // one thread per atom
     int blk_cell0, nblk_cell;  // one warp per cell
     int spec_index;            // index of this specimen in the launch table
+    int tiled;                 // pair passes by cell tiles (nblk_pair blocks loop over them)
+    int ntile_grid;            // tiles of the cell grid (ncell / 8)
     // lattice (creation only)
     int ncl[3];
     double a0, grip_width;
@@ -108,6 +125,8 @@ struct SpecDev {
     float4 *ref;    // positions at the last list build (skin test)
     int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
     int *orig;        // original index (creation order) of the atom stored at each slot
+    int *tile_list;   // tiled: occupied tiles in rank order (SpecCtl::ntiles of them)
+    int *tile_tab;    // tiled: TT_STRIDE ints per tile of the grid
     int *unit_first;  // G = 2: first slot of each unit | (1 << 30) when it has a second atom
     int *unit_cell;   // G = 2: first unit of each cell (ncell + 1)
     void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
@@ -125,7 +144,7 @@ struct SpecDev {
 };
 
 struct Group {
-    int prec, L, G, sc76;
+    int prec, L, G, sc76, tiled;
     const int *b2s;
     int nblk;
 };
@@ -169,21 +188,36 @@ __device__ __forceinline__ float nl_offz(unsigned e) {
     return __int_as_float(0x4B400000 | (int)(e & 0x1C0u)) - 12583104.0f;
 }
 
-// Cells are numbered along a serpentine path (x reverses on every other row,
-// y on every other layer), so that consecutive cells are face neighbours and
-// consecutive atoms of the cell-sorted order lie in the same or adjacent cells.
+// Cells are numbered tile by tile: the tiles of 2x2x2 cells (the grid has
+// an even number of cells per axis) follow a serpentine path (x reverses on
+// every other row, y on every other layer), and the 8 cells of a tile take
+// ranks 8t + (x & 1) + 2 (y & 1) + 4 (z & 1).  A tile's atoms are therefore
+// one contiguous range of the cell-sorted order, and consecutive tiles are
+// face neighbours.
 __host__ __device__ __forceinline__ int cell_rank(const int nc[3], int x, int y, int z) {
-    const int yr = (z & 1) ? nc[1] - 1 - y : y;
-    const int t = z * nc[1] + yr;
-    const int xr = (t & 1) ? nc[0] - 1 - x : x;
-    return t * nc[0] + xr;
+    const int n0 = nc[0] >> 1, n1 = nc[1] >> 1;
+    const int bx = x >> 1, by = y >> 1, bz = z >> 1;
+    const int byr = (bz & 1) ? n1 - 1 - by : by;
+    const int t = bz * n1 + byr;
+    const int bxr = (t & 1) ? n0 - 1 - bx : bx;
+    return ((t * n0 + bxr) << 3) | (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+}
+// tile coordinates of tile rank b
+__host__ __device__ __forceinline__ void tile_coords(const int nc[3], int b, int &bx, int &by,
+                                                     int &bz) {
+    const int n0 = nc[0] >> 1, n1 = nc[1] >> 1;
+    const int t = b / n0, bxr = b % n0;
+    bz = t / n1;
+    const int byr = t % n1;
+    by = (bz & 1) ? n1 - 1 - byr : byr;
+    bx = (t & 1) ? n0 - 1 - bxr : bxr;
 }
 __host__ __device__ __forceinline__ void cell_coords(const int nc[3], int r, int &x, int &y, int &z) {
-    const int t = r / nc[0], xr = r % nc[0];
-    z = t / nc[1];
-    const int yr = t % nc[1];
-    y = (z & 1) ? nc[1] - 1 - yr : yr;
-    x = (t & 1) ? nc[0] - 1 - xr : xr;
+    int bx, by, bz;
+    tile_coords(nc, r >> 3, bx, by, bz);
+    x = 2 * bx + (r & 1);
+    y = 2 * by + ((r >> 1) & 1);
+    z = 2 * bz + ((r >> 2) & 1);
 }
 
 // centre of the cell of rank r (exact in FP32: org on a 2^-12 grid, h a
@@ -297,6 +331,7 @@ __device__ __forceinline__ bool prune_active(const SpecDev &S, int force) {
     return S.ctl->phase != PH_IDLE && S.ctl->prune != 0;
 }
 void launch_density(const Tab &t, int force, cudaStream_t st);
+int tile_kernels_init();  // 0 when the tile kernels can use their shared memory
 void launch_force(const Tab &t, int mode, cudaStream_t st);
 
 }  // namespace pta
