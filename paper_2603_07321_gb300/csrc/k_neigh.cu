@@ -6,7 +6,7 @@
 // of edge >= rc + skin; atoms outside the grid are clamped onto its border
 // cells, which keeps every pair within reach (clamping is non-expansive).
 // After binning, the atoms themselves are permuted into cell order (cells in
-// rank order, atoms of a cell in their previous order), so that
+// rank order, atoms of a cell in creation order), so that
 // the 32 atoms of a warp share a cell and read overlapping neighbours, and a
 // cell's atoms are one contiguous range.  The list order (cell order, then
 // slot) is therefore a function of positions and grid: builds are
@@ -56,7 +56,7 @@ __global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__
     int ci[3];
     for (int d = 0; d < 3; ++d)
         ci[d] = clampi((int)floor((x[d] - S.org[d]) * S.inv_h), 0, S.nc[d] - 1);
-    const int c = cell_rank(S.nc, ci[0], ci[1], ci[2]);
+    const int c = cell_rank(S.tiled, S.nc, ci[0], ci[1], ci[2]);
     S.atom_cell[a] = c;
     atomicAdd(&S.cell_cnt[c], 1);
 }
@@ -205,7 +205,7 @@ __global__ void k_tile_table(const SpecDev *__restrict__ specs, const int *__res
             cnt[i] = 0;
             st[i] = 0;
             if (x >= 0 && y >= 0 && z >= 0 && x < S.nc[0] && y < S.nc[1] && z < S.nc[2]) {
-                const int c = cell_rank(S.nc, x, y, z);
+                const int c = cell_rank(S.tiled, S.nc, x, y, z);
                 st[i] = S.cell_start[c];
                 cnt[i] = S.cell_start[c + 1] - st[i];
             }
@@ -244,8 +244,10 @@ __global__ void k_scatter(const SpecDev *__restrict__ specs, const int *__restri
     S.cell_tmp[slot] = a;
 }
 
-// one warp per cell: order the cell's atoms by index (rank = number of
-// smaller indices), then clear the cell's counter for the next build
+// one warp per cell: order the cell's atoms by creation index (rank = number
+// of smaller ones), so that the order within a cell, and with it every list
+// order, does not depend on how cells are numbered; then clear the cell's
+// counter for the next build
 __global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
                             int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -256,8 +258,9 @@ __global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__rest
     const int s = S.cell_start[c], e = S.cell_start[c + 1];
     for (int p = s + lane; p < e; p += 32) {
         const int v = S.cell_tmp[p];
+        const int ov = S.orig[v];
         int r = 0;
-        for (int q = s; q < e; ++q) r += (S.cell_tmp[q] < v);
+        for (int q = s; q < e; ++q) r += (S.orig[S.cell_tmp[q]] < ov);
         S.cell_atoms[s + r] = v;
     }
     if (lane == 0) S.cell_cnt[c] = 0;
@@ -324,8 +327,11 @@ __global__ void k_unit_table(const SpecDev *__restrict__ specs, const int *__res
     S.unit_first[S.unit_cell[c] + r / 2] = p | ((r + 1 < cnt) ? UNIT_SECOND : 0);
 }
 
-// mixed precision: neighbour records of every atom relative to its new cell
-// (the build tests candidates with them, and the first density pass reads them)
+// mixed precision: every atom's half-cell in its new cell, its neighbour
+// record relative to that half-cell's centre (read by the pruning and the
+// first density pass), and in the scratch posfp its position relative to
+// the cell centre with the half-cell bits, spread onto the offset fields, in
+// w (read by the list build, which tests candidates cell by cell)
 __global__ void k_rel_all(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
                           int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -335,8 +341,14 @@ __global__ void k_rel_all(const SpecDev *__restrict__ specs, const int *__restri
     const int par = S.ctl->parity;
     const float4 h = ((const float4 *)S.pos[par])[a];
     const float4 l = S.lo[par][a];
-    const float3 C = cell_centre(S, S.atom_cell[a]);
-    S.rel[par][a] = make_float4((h.x - C.x) + l.x, (h.y - C.y) + l.y, (h.z - C.z) + l.z, 0.f);
+    const int c = S.atom_cell[a];
+    const float3 C = cell_centre(S, c);
+    const float cx = (h.x - C.x) + l.x, cy = (h.y - C.y) + l.y, cz = (h.z - C.z) + l.z;
+    const int sub = (cx >= 0.f ? 1 : 0) | (cy >= 0.f ? 2 : 0) | (cz >= 0.f ? 4 : 0);
+    S.hsub[a] = (uint8_t)sub;
+    ((float4 *)S.posfp)[a] = make_float4(cx, cy, cz, __int_as_float(sub_spread(sub)));
+    const float3 R = half_centre(S, c, sub);
+    S.rel[par][a] = make_float4((h.x - R.x) + l.x, (h.y - R.y) + l.y, (h.z - R.z) + l.z, 0.f);
 }
 
 constexpr int RW_ROWS = 48;
@@ -399,14 +411,17 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         // staged halo
         for (int r = 0; r < RW_ROWS; ++r) wr.buf[r * 32 + lane] = 0;
         __syncwarp();
-        const float4 ra = S.rel[par][a];
+        // cell-relative records with the spread half-cell bits in w (k_rel_all)
+        const float4 *__restrict__ crec = (const float4 *)S.posfp;
+        const float4 ra = crec[a];
+        const int own_sub = __float_as_int(ra.w);
         const float4 ha = ((const float4 *)S.pos[par])[a];
         const float4 la = S.lo[par][a];
         const double xa = (double)ha.x + (double)la.x, ya = (double)ha.y + (double)la.y,
                      za = (double)ha.z + (double)la.z;
         const int ca = S.atom_cell[a];
         int cx, cy, cz;
-        cell_coords(S.nc, ca, cx, cy, cz);
+        cell_coords(S.tiled, S.nc, ca, cx, cy, cz);
         // tiled: entries of a staged tile index its halo copy; halo cell of
         // the neighbour cell at offset d is (own cell in the tile + 1 + d)
         const int *__restrict__ Tt = S.tiled ? S.tile_tab + (long long)(ca >> 3) * TT_STRIDE : nullptr;
@@ -420,15 +435,16 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                     const bool inside = valid && xx >= 0 && yy >= 0 && zz >= 0 && xx < S.nc[0] &&
                                         yy < S.nc[1] && zz < S.nc[2];
                     if (inside) {
-                        const int cc = cell_rank(S.nc, xx, yy, zz);
+                        const int cc = cell_rank(S.tiled, S.nc, xx, yy, zz);
                         const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
-                        const unsigned code = nl_entry(0, dx, dy, dz);
+                        // half-cell offset 2d + sub_j - sub_a: add the spread bits of j
+                        const unsigned code = nl_entry(0, 2 * dx, 2 * dy, 2 * dz) - (unsigned)own_sub;
                         const int shift = staged ? Tt[TT_OFF + hown + dx + 4 * dy + 16 * dz] - s : 0;
                         // position of atom a relative to the centre of cell cc
                         const float ox = ra.x - (float)dx * h, oy = ra.y - (float)dy * h,
                                     oz = ra.z - (float)dz * h;
                         for (int j = s; j < e; ++j) {
-                            const float4 rj = S.rel[par][j];
+                            const float4 rj = crec[j];
                             const float fx = rj.x - ox, fy = rj.y - oy, fz = rj.z - oz;
                             const float r2f = fx * fx + fy * fy + fz * fz;
                             bool in;
@@ -440,7 +456,8 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                                 in = in_list(S, par, true, a, xa, ya, za, ha, la, j);
                             if (in && j != a) {
                                 if (cnt < S.cap_use)
-                                    wr.put(cnt, (int)(((unsigned)(j + shift) << NL_CODE_BITS) | code));
+                                    wr.put(cnt, (int)(((unsigned)(j + shift) << NL_CODE_BITS) +
+                                                      code + (unsigned)__float_as_int(rj.w)));
                                 ++cnt;
                             }
                         }
@@ -471,7 +488,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                 ha[g] = ((const float4 *)S.pos[par])[a0 + g];
                 la[g] = S.lo[par][a0 + g];
             }
-            cell_coords(S.nc, S.atom_cell[a0 + g], cx[g], cy[g], cz[g]);
+            cell_coords(S.tiled, S.nc, S.atom_cell[a0 + g], cx[g], cy[g], cz[g]);
         }
         int lo[3] = {cx[0], cy[0], cz[0]}, hi[3] = {cx[0], cy[0], cz[0]};
         for (int g = 1; g < ga; ++g) {
@@ -484,36 +501,34 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         }
         const long long base = nl_base(u, S.L, S.cap);
         const int L = S.L;
+        // mixed: half-cell offsets from the unit's first atom (its atoms share a cell)
+        const int sub0 = mixed ? sub_spread(S.hsub[a0]) : 0;
         for (int zz = max(lo[2] - 1, 0); zz <= min(hi[2] + 1, S.nc[2] - 1); ++zz)
             for (int yy = max(lo[1] - 1, 0); yy <= min(hi[1] + 1, S.nc[1] - 1); ++yy)
                 for (int xx = max(lo[0] - 1, 0); xx <= min(hi[0] + 1, S.nc[0] - 1); ++xx) {
-                    const int cc = cell_rank(S.nc, xx, yy, zz);
+                    const int cc = cell_rank(S.tiled, S.nc, xx, yy, zz);
                     const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
-                    const unsigned code = nl_entry(0, xx - cx[0], yy - cy[0], zz - cz[0]);
+                    const unsigned code =
+                        mixed ? nl_entry(0, 2 * (xx - cx[0]), 2 * (yy - cy[0]), 2 * (zz - cz[0])) -
+                                    (unsigned)sub0
+                              : nl_entry(0, xx - cx[0], yy - cy[0], zz - cz[0]);
                     for (int j = s; j < e; ++j) {
                         bool in = false;
                         for (int g = 0; g < ga && !in; ++g)
                             in = (j != a0 + g) && in_list(S, par, mixed, a0 + g, x[g], y[g], z[g],
                                                           ha[g], la[g], j);
                         if (in) {
+                            const unsigned cj = mixed ? code + (unsigned)sub_spread(S.hsub[j]) : code;
                             if (cnt < S.cap_use)
                                 S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
-                                    (int)(((unsigned)j << NL_CODE_BITS) | code);
+                                    (int)(((unsigned)j << NL_CODE_BITS) + cj);
                             ++cnt;
                         }
                     }
                 }
         S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
-        for (int g = 0; g < ga; ++g) {
-            const int a = a0 + g;
-            S.ref[a] = make_float4((float)x[g], (float)y[g], (float)z[g], 0.f);
-            if (mixed) {
-                // the neighbour-visible record relative to the (new) cell centre
-                const float3 C = cell_centre(S, S.atom_cell[a]);
-                S.rel[par][a] = make_float4((ha[g].x - C.x) + la[g].x, (ha[g].y - C.y) + la[g].y,
-                                            (ha[g].z - C.z) + la[g].z, 0.f);
-            }
-        }
+        for (int g = 0; g < ga; ++g)
+            S.ref[a0 + g] = make_float4((float)x[g], (float)y[g], (float)z[g], 0.f);
     }
     // block maximum of the counts, one atomic per block
     __shared__ int smax[TPB / 32];

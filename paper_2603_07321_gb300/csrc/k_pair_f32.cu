@@ -2,9 +2,10 @@
 // on relative coordinates.  Positions are kept as an exact FP32 pair
 // x = hi + lo (hi on a 2^-12 A grid, |lo| <= 2^-13 A) for the integration;
 // what a neighbour reads is one 16-byte record, the position relative to the
-// centre of its cell, rel = (hi - C) + lo, so that with the cell offset d
-// coded in the list entry
-//     r_j - r_i = (rel_j - rel_i) + h d
+// centre C of its half-cell (one of the 8 octants of its cell, fixed at the
+// list build), rel = (hi - C) + lo with |rel| <= h / 4 + skin / 2, so that
+// with the half-cell offset d coded in the list entry
+//     r_j - r_i = (rel_j - rel_i) + (h / 2) d
 // (C and h on exact grids).  Velocities FP32; energies, stresses and time
 // averages reduced in FP64.
 //
@@ -48,6 +49,16 @@ struct PowF {
     }
 };
 
+// 1 / sqrt(r2): the hardware estimate refined by one Newton-Raphson step
+// y' = y + y (1 - r2 y^2) / 2 (the residual formed with a fused multiply-add),
+// which brings it to about one unit in the last place; the pair terms raise
+// s = a / r to the 6th and 7th power, which multiplies its relative error
+__device__ __forceinline__ float rsqrt_nr(float r2) {
+    const float y = rsqrtf(r2);
+    const float e = fmaf(-(r2 * y), y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+}
+
 // The unit of work is one atom (G = 1) or two atoms of one cell (G = 2)
 // sharing one neighbour list (the union of their lists), handled by L lanes.
 // For every entry the displacement from the unit's first atom is formed
@@ -72,6 +83,16 @@ __device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, in
     return (const unsigned *)S.nlist + off;
 }
 
+// offset of a unit's second atom from its first: they share a cell, their
+// half-cells may differ by h / 2 along an axis
+__device__ __forceinline__ float3 unit_dg(const SpecDev &S, int a0, float4 r0, float4 r1) {
+    const int s0 = S.hsub[a0], s1 = S.hsub[a0 + 1];
+    const float q = S.f_q;
+    return make_float3(fmaf((float)((s1 & 1) - (s0 & 1)), q, r1.x - r0.x),
+                       fmaf((float)(((s1 >> 1) & 1) - ((s0 >> 1) & 1)), q, r1.y - r0.y),
+                       fmaf((float)((s1 >> 2) - (s0 >> 2)), q, r1.z - r0.z));
+}
+
 // displacement of entry e's atom (record x) from the unit's first atom (record r0)
 __device__ __forceinline__ float3 entry_disp(unsigned e, float4 x, float4 r0, float h, float h8,
                                              float h64) {
@@ -89,7 +110,7 @@ struct DensityAcc {
             const float ex = d.x - dg[g].x, ey = d.y - dg[g].y, ez = d.z - dg[g].z;
             const float r2 = ex * ex + ey * ey + ez * ez;
             if (r2 < rc2 && (G == 1 || (r2 > 0.f && g < ga))) {
-                const float ir = rsqrtf(r2);
+                const float ir = rsqrt_nr(r2);
                 const float s = S.pot.f_a * ir;
                 rho[g] += PowF<SC76>::pm(s, S.pot.m) - S.pot.f_Am + S.pot.f_Bm * (r2 * ir - S.pot.f_rc);
             }
@@ -108,7 +129,7 @@ struct ForceAcc {
             const float ex = d.x - dg[g].x, ey = d.y - dg[g].y, ez = d.z - dg[g].z;
             const float r2 = ex * ex + ey * ey + ez * ez;
             if (r2 < rc2 && (G == 1 || (r2 > 0.f && g < ga))) {
-                const float ir = rsqrtf(r2);
+                const float ir = rsqrt_nr(r2);
                 const float r = r2 * ir;
                 const float s = S.pot.f_a * ir;
                 float sn, sm;
@@ -183,7 +204,7 @@ __device__ __forceinline__ void atom_update(const SpecDev &S, SpecCtl *ctl, int 
     }
     ((float4 *)S.pos[par ^ 1])[a] = make_float4(hh[0], hh[1], hh[2], 0.f);
     S.lo[par ^ 1][a] = make_float4(qq[0], qq[1], qq[2], 0.f);
-    const float3 C = cell_centre(S, S.atom_cell[a]);
+    const float3 C = half_centre(S, S.atom_cell[a], S.hsub[a]);
     S.rel[par ^ 1][a] = make_float4((hh[0] - C.x) + qq[0], (hh[1] - C.y) + qq[1],
                                     (hh[2] - C.z) + qq[2], 0.f);
     ((float4 *)S.vel)[a] = v;
@@ -211,7 +232,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
     const int l = threadIdx.x % L;
     const bool valid = u < ctl->nunits;
     const float4 *__restrict__ rel = S.rel[par];
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
     int a0 = 0, ga = 0;
     if (valid) unit_atoms(S, u, a0, ga);
     DensityAcc<G, SC76> acc;
@@ -228,7 +249,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
         for (int g = 0; g < G; ++g)
             if (g < ga) ra[g] = rel[a0 + g];
         if (G > 1 && ga > 1)  // both atoms share a cell: the offset is rel_1 - rel_0
-            dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+            dg[1] = unit_dg(S, a0, ra[0], ra[1]);
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
@@ -270,7 +291,7 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
     const int l = threadIdx.x % L;
     const bool valid = u < ctl->nunits;
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
     int a0 = 0, ga = 0;
     if (valid) unit_atoms(S, u, a0, ga);
     ForceAcc<G, SC76> acc;
@@ -287,7 +308,7 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
         for (int g = 0; g < G; ++g)
             if (g < ga) ra[g] = lf[a0 + g];
         if (G > 1 && ga > 1)
-            dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+            dg[1] = unit_dg(S, a0, ra[0], ra[1]);
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
     const int l = threadIdx.x % L;
     if (u >= ctl->nunits) return;
     const float4 *__restrict__ rel = S.rel[par];
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64, rp2 = S.f_rp2;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64, rp2 = S.f_rp2;
     int a0, ga;
     unit_atoms(S, u, a0, ga);
     float4 ra[G];
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
     for (int g = 0; g < G; ++g)
         if (g < ga) ra[g] = rel[a0 + g];
     if (G > 1 && ga > 1)
-        dg[1] = make_float3(ra[1].x - ra[0].x, ra[1].y - ra[0].y, ra[1].z - ra[0].z);
+        dg[1] = unit_dg(S, a0, ra[0], ra[1]);
     const long long off = nl_base(u, L, S.cap) + l;
     const unsigned *__restrict__ src = (const unsigned *)S.nlist + off;
     unsigned *__restrict__ dst = (unsigned *)S.plist + off;
@@ -430,7 +451,7 @@ template <bool SC76, bool ST>
 __device__ __forceinline__ float tile_rho(const SpecDev &S, const float4 *__restrict__ rel,
                                           const float4 *stg, const unsigned *__restrict__ lst,
                                           int cl, float4 r0) {
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
     const float3 dg0 = make_float3(0.f, 0.f, 0.f);
     DensityAcc<1, SC76> acc;
     acc.rho[0] = 0.f;
@@ -451,7 +472,7 @@ template <bool SC76, bool ST>
 __device__ __forceinline__ void tile_force(const SpecDev &S, const float4 *__restrict__ lf,
                                            const float4 *stg, const unsigned *__restrict__ lst,
                                            int cl, float4 r0, ForceAcc<1, SC76> &acc) {
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
     const float3 dg0 = make_float3(0.f, 0.f, 0.f);
     unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
     for (int q = 0; q < cl; q += 2) {
@@ -553,7 +574,7 @@ __global__ void __launch_bounds__(TILE_T, 3) k_prune_tile(const SpecDev *__restr
     const SpecCtl *ctl = S.ctl;
     const int par = ctl->parity;
     const float4 *__restrict__ rel = S.rel[par];
-    const float h = S.f_h, h8 = S.f_h8, h64 = S.f_h64, rp2 = S.f_rp2;
+    const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64, rp2 = S.f_rp2;
     const int nt = ctl->ntiles;
     for (int k = blockIdx.x - S.blk_pair0; k < nt; k += S.nblk_pair) {
         const int *__restrict__ T = S.tile_tab + (long long)__ldg(S.tile_list + k) * TT_STRIDE;

@@ -359,6 +359,7 @@ static size_t footprint(const Sizes &z, int prec) {
         add(16 * n);                 // lo[2]
         add(16 * n);
         add(16 * n);                 // rel[2]
+        add(n);                      // hsub
     }
     add(p * n);                      // posfp
     add(p * n);                      // vel
@@ -975,6 +976,7 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
         AL(lo[1], 16 * n, float4 *);
         AL(rel[0], 16 * n, float4 *);
         AL(rel[1], 16 * n, float4 *);
+        AL(hsub, n, uint8_t *);
     }
     AL(posfp, p * n, void *);
     AL(vel, p * n, void *);
@@ -1067,8 +1069,9 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.inv_h = 1.0 / z.h;
     s.f_inv_h = (float)s.inv_h;
     s.f_h = (float)z.h;
-    s.f_h8 = (float)(z.h / 8.0);
-    s.f_h64 = (float)(z.h / 64.0);
+    s.f_q = (float)(z.h / 2.0);
+    s.f_q8 = (float)(z.h / 16.0);
+    s.f_q64 = (float)(z.h / 128.0);
     s.ncell = z.ncell;
     const double rl = c->pot.rc + c->par.skin;
     s.rl2 = rl * rl;

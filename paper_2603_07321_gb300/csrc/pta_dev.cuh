@@ -105,7 +105,8 @@ struct SpecDev {
     int ncell;
     // list radius (rc + skin)^2 and its FP32 bracket; half skin squared
     double rl2;
-    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h, f_h, f_h8, f_h64;
+    float f_rl2_lo, f_rl2_hi, half_skin2, f_inv_h, f_h;
+    float f_q, f_q8, f_q64;  // half the cell edge (unit of the list offsets), / 8, / 64
     float f_org[3];
     PotDev pot;
     // integration constants
@@ -118,8 +119,10 @@ struct SpecDev {
     void *pos[2];   // FP64: double4 {x,y,z,0};  MIXED: float4 hi {x,y,z,0}
     float4 *lo[2];  // MIXED only: float4 lo {x,y,z,0}
     void *posfp;    // FP64: double4 {x,y,z,F'(rho)};  MIXED: float4 {rel.xyz, F'(rho)}
-    float4 *rel[2]; // MIXED only: position relative to the centre of its cell (FP32):
-                    // the 16-byte record the pair passes read for a neighbour
+    float4 *rel[2]; // MIXED only: position relative to the centre of its half-cell
+                    // (FP32): the 16-byte record the pair passes read for a neighbour
+    uint8_t *hsub;  // MIXED only: half-cell of each atom in its cell (bit d: upper half
+                    // along axis d), fixed from one list build to the next
     void *vel;      // FP64: double4; MIXED: float4
     uint8_t *flags;
     float4 *ref;    // positions at the last list build (skin test)
@@ -162,10 +165,12 @@ struct Tab {
 };
 
 // Verlet-list entry (one list per unit): neighbour index in the high 23
-// bits, the neighbour's cell offset (dx, dy, dz) relative to the cell of the
-// unit's first atom in the low 9 bits, 3 bits per axis holding d + 3.  With
-// cell centres and the cell edge h on exact grids,
-// r_j - r_i = (rel_j - rel_i) + h * d.
+// bits, an offset (dx, dy, dz) in the low 9 bits, 3 bits per axis holding
+// d + 3.  In mixed precision d is the offset of the neighbour's half-cell
+// from the half-cell of the unit's first atom in units of h / 2 (within the
+// 3x3x3 cells around a cell, |d| <= 3); with half-cell centres and h on
+// exact grids, r_j - r_i = (rel_j - rel_i) + (h / 2) d.  FP64 lists keep
+// whole-cell offsets, which its kernels do not read.
 constexpr int NL_CODE_BITS = 9;
 constexpr int MAX_ATOMS = 1 << 23;
 
@@ -188,31 +193,42 @@ __device__ __forceinline__ float nl_offz(unsigned e) {
     return __int_as_float(0x4B400000 | (int)(e & 0x1C0u)) - 12583104.0f;
 }
 
-// Cells are numbered tile by tile: the tiles of 2x2x2 cells (the grid has
-// an even number of cells per axis) follow a serpentine path (x reverses on
-// every other row, y on every other layer), and the 8 cells of a tile take
-// ranks 8t + (x & 1) + 2 (y & 1) + 4 (z & 1).  A tile's atoms are therefore
-// one contiguous range of the cell-sorted order, and consecutive tiles are
-// face neighbours.
-__host__ __device__ __forceinline__ int cell_rank(const int nc[3], int x, int y, int z) {
-    const int n0 = nc[0] >> 1, n1 = nc[1] >> 1;
-    const int bx = x >> 1, by = y >> 1, bz = z >> 1;
-    const int byr = (bz & 1) ? n1 - 1 - by : by;
-    const int t = bz * n1 + byr;
-    const int bxr = (t & 1) ? n0 - 1 - bx : bx;
-    return ((t * n0 + bxr) << 3) | (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+// Cells are numbered along a serpentine path (x reverses on every other row,
+// y on every other layer), so that consecutive cells are face neighbours and
+// consecutive atoms of the cell-sorted order lie in the same or adjacent
+// cells.  With cell tiles (tm = 1) the same path runs over tiles of 2x2x2
+// cells (the grid has an even number of cells per axis) and the 8 cells of
+// tile t take ranks 8t + (x & 1) + 2 (y & 1) + 4 (z & 1), so that a tile's
+// atoms are one contiguous range.
+__host__ __device__ __forceinline__ int serp_rank(int n0, int n1, int x, int y, int z) {
+    const int yr = (z & 1) ? n1 - 1 - y : y;
+    const int t = z * n1 + yr;
+    const int xr = (t & 1) ? n0 - 1 - x : x;
+    return t * n0 + xr;
 }
-// tile coordinates of tile rank b
+__host__ __device__ __forceinline__ void serp_coords(int n0, int n1, int r, int &x, int &y, int &z) {
+    const int t = r / n0, xr = r % n0;
+    z = t / n1;
+    const int yr = t % n1;
+    y = (z & 1) ? n1 - 1 - yr : yr;
+    x = (t & 1) ? n0 - 1 - xr : xr;
+}
+__host__ __device__ __forceinline__ int cell_rank(int tm, const int nc[3], int x, int y, int z) {
+    if (!tm) return serp_rank(nc[0], nc[1], x, y, z);
+    return (serp_rank(nc[0] >> 1, nc[1] >> 1, x >> 1, y >> 1, z >> 1) << 3) | (x & 1) |
+           ((y & 1) << 1) | ((z & 1) << 2);
+}
+// tile coordinates of tile rank b (tile-major numbering)
 __host__ __device__ __forceinline__ void tile_coords(const int nc[3], int b, int &bx, int &by,
                                                      int &bz) {
-    const int n0 = nc[0] >> 1, n1 = nc[1] >> 1;
-    const int t = b / n0, bxr = b % n0;
-    bz = t / n1;
-    const int byr = t % n1;
-    by = (bz & 1) ? n1 - 1 - byr : byr;
-    bx = (t & 1) ? n0 - 1 - bxr : bxr;
+    serp_coords(nc[0] >> 1, nc[1] >> 1, b, bx, by, bz);
 }
-__host__ __device__ __forceinline__ void cell_coords(const int nc[3], int r, int &x, int &y, int &z) {
+__host__ __device__ __forceinline__ void cell_coords(int tm, const int nc[3], int r, int &x, int &y,
+                                                     int &z) {
+    if (!tm) {
+        serp_coords(nc[0], nc[1], r, x, y, z);
+        return;
+    }
     int bx, by, bz;
     tile_coords(nc, r >> 3, bx, by, bz);
     x = 2 * bx + (r & 1);
@@ -224,10 +240,25 @@ __host__ __device__ __forceinline__ void cell_coords(const int nc[3], int r, int
 // multiple of 2^-11)
 __device__ __forceinline__ float3 cell_centre(const SpecDev &S, int r) {
     int cx, cy, cz;
-    cell_coords(S.nc, r, cx, cy, cz);
+    cell_coords(S.tiled, S.nc, r, cx, cy, cz);
     return make_float3(S.f_org[0] + ((float)cx + 0.5f) * S.f_h,
                        S.f_org[1] + ((float)cy + 0.5f) * S.f_h,
                        S.f_org[2] + ((float)cz + 0.5f) * S.f_h);
+}
+
+// centre of half-cell `sub` of the cell of rank r: the cell centre moved by
+// -h/4 or +h/4 per axis (exact in FP32: on a 2^-13 A grid)
+__device__ __forceinline__ float3 half_centre(const SpecDev &S, int r, int sub) {
+    float3 C = cell_centre(S, r);
+    const float q = 0.25f * S.f_h;
+    C.x += (sub & 1) ? q : -q;
+    C.y += (sub & 2) ? q : -q;
+    C.z += (sub & 4) ? q : -q;
+    return C;
+}
+// the 3 half-cell bits spread onto the 3 offset fields of a list entry
+__host__ __device__ __forceinline__ int sub_spread(int sub) {
+    return (sub & 1) | ((sub & 2) << 2) | ((sub & 4) << 4);
 }
 
 // segments of the permutation scratch (see perm_layout)

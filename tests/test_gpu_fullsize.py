@@ -1,16 +1,16 @@
 """Parity at the full benchmark size, in the launch configuration bench.py
 times: the 49^3-cell cube (470,596 atoms), mixed precision, automatic lanes.
-The oracle evaluates the forces of sampled atoms one by one."""
+The oracle evaluates the forces of every atom."""
 import numpy as np
 import pytest
 
 import pta_inputs as PI
-from gpu_util import gpu_package, on_grid
+from gpu_util import force_error, force_error_atom, force_error_rms, gpu_package, on_grid
 
 pytestmark = pytest.mark.gpu
 
 
-def test_sampled_forces_on_the_470596_atom_cube(oracle):
+def test_forces_of_every_atom_of_the_470596_atom_cube(oracle):
     P = gpu_package()
     n = 49
     pos = on_grid(PI.gaussian_jitter_fcc(n, 0.1, seed=49))
@@ -18,19 +18,21 @@ def test_sampled_forces_on_the_470596_atom_cube(oracle):
     assert ctx.n == 470596
     ctx.set_state(pos, np.zeros_like(pos))
     f, pe, _ = ctx.forces()
-    rng = np.random.default_rng(5)
-    idx = np.sort(rng.choice(ctx.n, 256, replace=False))
-    # include grip atoms and surface atoms explicitly
-    fl = ctx.flags()
-    idx = np.unique(np.concatenate([idx, np.flatnonzero(fl == 2)[:16], np.flatnonzero(fl == 1)[:16],
-                                    [0, ctx.n - 1]]))
     p = ctx.potential
     pot = oracle.Potential(eps=p.eps, c=p.c, a=p.a, rc=p.rc, n=p.n, m=p.m)
-    f_ref, pe_ref = oracle.eam_sampled(pos, pot, idx)
-    scale = np.sqrt(np.mean(np.sum(f_ref ** 2, axis=1)))
-    err = np.max(np.linalg.norm(f[idx] - f_ref, axis=1)) / scale
-    assert err < 1e-5, err
-    assert np.max(np.abs(pe[idx] - pe_ref) / np.abs(pe_ref)) < 1e-5
+    f_ref, pe_ref, _ = oracle.eam(pos, pot)
+    # every atom's force to 1e-5 of itself (floored at the rms force), the
+    # rms error to 3e-6; atoms pushed into close pairs carry forces of ~5x
+    # the rms, and their absolute errors reach ~1.5e-5 of the rms force
+    assert force_error_atom(f, f_ref) < 1e-5
+    assert force_error_rms(f, f_ref) < 3e-6
+    assert force_error(f, f_ref) < 3e-5
+    assert np.max(np.abs(pe - pe_ref) / np.abs(pe_ref)) < 1e-5
+    # the sampled one-by-one evaluation agrees with the full one
+    idx = np.unique(np.concatenate([np.random.default_rng(5).choice(ctx.n, 64, replace=False),
+                                    np.flatnonzero(ctx.flags() == 2)[:8], [0, ctx.n - 1]]))
+    fs, pes = oracle.eam_sampled(pos, pot, idx)
+    assert np.allclose(fs, f_ref[idx], rtol=1e-12, atol=1e-12)
     ctx.close()
 
 

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import pta_inputs as PI
-from gpu_util import force_error, gpu_package, on_grid, sorted_rows
+from gpu_util import force_error_atom, gpu_package, on_grid, sorted_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -44,9 +44,8 @@ def test_tiled_forces_identical_to_untiled_and_match_oracle(P, oracle):
     assert np.array_equal(f1, f0) and np.array_equal(pe1, pe0)
     # U sums the same per-atom energies in other FP32 warp groups
     assert np.allclose(obs1, obs0, rtol=1e-6, atol=1e-9)
-    # the shared arithmetic against the oracle: within the FP32 bound
     f_ref, pe_ref, _ = oracle.eam(pos, oracle.Potential())
-    assert force_error(f1, f_ref) < 3e-5
+    assert force_error_atom(f1, f_ref) < 1e-5
     assert np.max(np.abs(pe1 - pe_ref) / np.abs(pe_ref)) < 1e-5
 
 
@@ -61,7 +60,7 @@ def test_dense_halo_reads_global_memory_with_identical_results(P, oracle):
     assert 0 < info["staged_tiles"] < info["tiles"]
     assert np.array_equal(f1, f0) and np.array_equal(pe1, pe0)
     f_ref, _, _ = oracle.eam(pos, oracle.Potential())
-    assert force_error(f1, f_ref) < 3e-5
+    assert force_error_atom(f1, f_ref) < 1e-5
 
 
 def test_tiled_trajectory_identical_to_untiled(P, oracle):
