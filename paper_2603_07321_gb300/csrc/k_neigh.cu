@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         const bool staged = Tt != nullptr && Tt[TT_STAGED] != 0;
         const int hown = (1 + (ca & 1)) + 4 * (1 + ((ca >> 1) & 1)) + 16 * (1 + ((ca >> 2) & 1));
         const float h = S.f_h;
-        for (int dz = -1; dz <= 1; ++dz)
+        // a warp past the last atom writes nothing: its tile lies beyond the
+        // list (and the rows every lane has passed are unbounded)
+        const bool wvalid = __any_sync(0xffffffffu, valid);
+        for (int dz = -1; dz <= 1 && wvalid; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int xx = cx + dx, yy = cy + dy, zz = cz + dz;
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                                  wr.flushed + RW_ROWS));
                 }
         const int top = __reduce_max_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 0);
-        wr.flush(top);
+        if (wvalid) wr.flush(top);
         if (valid) {
             // the row after the last entry is read (and gathered) by the
             // unrolled pair loops: a filler entry

@@ -41,3 +41,26 @@ def test_results_are_the_same_alone_and_in_the_mix():
             assert s1 == s2 and v1 == v2 and src1 == src2   # bit-identical
     st = s.stats()
     assert st["done"] == 3 and st["coarse_step_latency_s"]["p99"] > 0
+
+
+def test_batch_of_uneven_served_sizes_stays_finite():
+    # sizes of a served trace (10..48 cells, mixed temperatures, tension and
+    # compression); several have a last thread block whose trailing warps
+    # hold no atom, which must write nothing beyond their lists
+    import pta_inputs as PI
+    P = gpu_package()
+    trace = PI.served_trace(8, seed=7)
+    ctxs = [P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=P.PREC_MIXED,
+                  burst_steps=r.burst_steps, strain_rate=r.strain_rate) for r in trace]
+    assert any((c.n % 128) and (c.n % 128) <= 96 for c in ctxs)
+    b = P.Batch(ctxs)
+    for _ in range(3):
+        b.apply_strain([1e-5] * len(ctxs))
+        res = b.fine_burst([200] * len(ctxs))
+        assert all(a.status == 0 and a.nsteps == 200 for a in res)
+    for c in ctxs:
+        p, v = c.get_state()
+        assert np.isfinite(p).all() and np.isfinite(v).all()
+    b.close()
+    for c in ctxs:
+        c.close()
