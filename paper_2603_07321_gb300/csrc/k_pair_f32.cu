@@ -7,7 +7,10 @@
 // with the half-cell offset d coded in the list entry
 //     r_j - r_i = (rel_j - rel_i) + (h / 2) d
 // (C and h on exact grids).  Velocities FP32; energies, stresses and time
-// averages reduced in FP64.
+// averages reduced in FP64.  The one-atom loops take two entries per
+// iteration and decode both offsets with packed FP32 instructions (two
+// lanes of one instruction, sm_100 family); the density pass also forms
+// both pair terms packed, then adds them to its sum in entry order.
 //
 // Pass 1 (density): rho_i = sum_j phi_m(r_ij), then B'(rho_i) =
 // -eps c / (2 sqrt(rho_i)) stored beside lo_i.  Eq. (pe).
@@ -100,9 +103,54 @@ __device__ __forceinline__ float3 entry_disp(unsigned e, float4 x, float4 r0, fl
                        fmaf(nl_offz(e), h64, x.z - r0.z));
 }
 
+// packed FP32 (two lanes of one instruction), round to nearest
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 rsqrt2_nr(float2 r2) {
+    // rsqrt_nr on both halves: y' = y + (-y/2) (r2 y y - 1), the same
+    // operations and roundings as the scalar form
+    const float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 e = __ffma2_rn(__fmul2_rn(r2, y), y, f2(-1.0f));
+    return __ffma2_rn(__fmul2_rn(y, f2(-0.5f)), e, y);
+}
+// displacements of two entries from the unit's first atom, packed by axis
+__device__ __forceinline__ void entry_disp2(unsigned ea, unsigned eb, float4 xa, float4 xb, float4 r0,
+                                            float h, float h8, float h64, float2 &dx, float2 &dy,
+                                            float2 &dz) {
+    const float2 ox = __fadd2_rn(make_float2(__int_as_float(0x4B400000 | (int)(ea & 0x7u)),
+                                             __int_as_float(0x4B400000 | (int)(eb & 0x7u))),
+                                 f2(-12582915.0f));
+    const float2 oy = __fadd2_rn(make_float2(__int_as_float(0x4B400000 | (int)(ea & 0x38u)),
+                                             __int_as_float(0x4B400000 | (int)(eb & 0x38u))),
+                                 f2(-12582936.0f));
+    const float2 oz = __fadd2_rn(make_float2(__int_as_float(0x4B400000 | (int)(ea & 0x1C0u)),
+                                             __int_as_float(0x4B400000 | (int)(eb & 0x1C0u))),
+                                 f2(-12583104.0f));
+    dx = __ffma2_rn(ox, f2(h), __fadd2_rn(make_float2(xa.x, xb.x), f2(-r0.x)));
+    dy = __ffma2_rn(oy, f2(h8), __fadd2_rn(make_float2(xa.y, xb.y), f2(-r0.y)));
+    dz = __ffma2_rn(oz, f2(h64), __fadd2_rn(make_float2(xa.z, xb.z), f2(-r0.z)));
+}
+
 template <int G, bool SC76>
 struct DensityAcc {
     float rho[G];
+    // one atom, the Sutton-Chen (7, 6) exponents: entries a and b (b only
+    // when vb) in the two halves of packed instructions; the terms within rc
+    // are added to the sum in entry order
+    __device__ __forceinline__ void add2(const SpecDev &S, float2 dx, float2 dy, float2 dz, bool vb) {
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 ir = rsqrt2_nr(r2);
+        const float2 s = __fmul2_rn(f2(S.pot.f_a), ir);
+        const float2 s2 = __fmul2_rn(s, s);
+        const float2 s3 = __fmul2_rn(s2, s);
+        const float2 s6 = __fmul2_rn(s3, s3);
+        const float2 u = __fadd2_rn(__fmul2_rn(r2, ir), f2(-S.pot.f_rc));
+        const float2 phi = __ffma2_rn(f2(S.pot.f_Bm), u, __fadd2_rn(s6, f2(-S.pot.f_Am)));
+        const float rc2 = S.pot.f_rc2;
+        if (r2.x < rc2) rho[0] += phi.x;
+        if (vb && r2.y < rc2) rho[0] += phi.y;
+    }
     __device__ __forceinline__ void add(const SpecDev &S, float3 d, const float3 *dg, int ga) {
         const float rc2 = S.pot.f_rc2;
 #pragma unroll
@@ -257,8 +305,14 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
             const float4 xa = __ldg(rel + nl_j(ea));
             const float4 xb = __ldg(rel + nl_j(eb));
-            acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), dg, ga);
-            if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), dg, ga);
+            if constexpr (G == 1 && SC76) {
+                float2 dx, dy, dz;
+                entry_disp2(ea, eb, xa, xb, ra[0], h, h8, h64, dx, dy, dz);
+                acc.add2(S, dx, dy, dz, q + 1 < cl);
+            } else {
+                acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), dg, ga);
+                if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), dg, ga);
+            }
             ea = na;
             eb = nb;
         }
@@ -316,8 +370,17 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
             const float4 xa = __ldg(lf + nl_j(ea));
             const float4 xb = __ldg(lf + nl_j(eb));
-            acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), xa.w, dg, ra, ga);
-            if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), xb.w, dg, ra, ga);
+            if constexpr (G == 1) {
+                // the offsets of both entries decoded in packed instructions;
+                // the pair terms stay scalar (packed, they measured slower here)
+                float2 dx, dy, dz;
+                entry_disp2(ea, eb, xa, xb, ra[0], h, h8, h64, dx, dy, dz);
+                acc.add(S, make_float3(dx.x, dy.x, dz.x), xa.w, dg, ra, ga);
+                if (q + 1 < cl) acc.add(S, make_float3(dx.y, dy.y, dz.y), xb.w, dg, ra, ga);
+            } else {
+                acc.add(S, entry_disp(ea, xa, ra[0], h, h8, h64), xa.w, dg, ra, ga);
+                if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, ra[0], h, h8, h64), xb.w, dg, ra, ga);
+            }
             ea = na;
             eb = nb;
         }
@@ -460,8 +523,14 @@ __device__ __forceinline__ float tile_rho(const SpecDev &S, const float4 *__rest
         const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
         const float4 xa = tile_rec<ST>(rel, stg, ea);
         const float4 xb = tile_rec<ST>(rel, stg, eb);
-        acc.add(S, entry_disp(ea, xa, r0, h, h8, h64), &dg0, 1);
-        if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, r0, h, h8, h64), &dg0, 1);
+        if constexpr (SC76) {
+            float2 dx, dy, dz;
+            entry_disp2(ea, eb, xa, xb, r0, h, h8, h64, dx, dy, dz);
+            acc.add2(S, dx, dy, dz, q + 1 < cl);
+        } else {
+            acc.add(S, entry_disp(ea, xa, r0, h, h8, h64), &dg0, 1);
+            if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, r0, h, h8, h64), &dg0, 1);
+        }
         ea = na;
         eb = nb;
     }
@@ -479,8 +548,10 @@ __device__ __forceinline__ void tile_force(const SpecDev &S, const float4 *__res
         const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
         const float4 xa = tile_rec<ST>(lf, stg, ea);
         const float4 xb = tile_rec<ST>(lf, stg, eb);
-        acc.add(S, entry_disp(ea, xa, r0, h, h8, h64), xa.w, &dg0, &r0, 1);
-        if (q + 1 < cl) acc.add(S, entry_disp(eb, xb, r0, h, h8, h64), xb.w, &dg0, &r0, 1);
+        float2 dx, dy, dz;
+        entry_disp2(ea, eb, xa, xb, r0, h, h8, h64, dx, dy, dz);
+        acc.add(S, make_float3(dx.x, dy.x, dz.x), xa.w, &dg0, &r0, 1);
+        if (q + 1 < cl) acc.add(S, make_float3(dx.y, dy.y, dz.y), xb.w, &dg0, &r0, 1);
         ea = na;
         eb = nb;
     }
