@@ -29,10 +29,11 @@ __device__ __forceinline__ T lane_sum(T v) {
 }
 
 // Called by every thread of a pair block of NT threads after the warp
-// reductions (values valid in lane 0 of each warp); red is shared scratch of
-// 5 NT doubles.  Block partials go to S.part (8 doubles per block); the last
-// block of the specimen to finish sums all partials in a fixed order and
-// advances the specimen's control block:
+// reductions (values valid in lane 0 of each warp).  Block partials go to
+// S.part (8 doubles per block); the last block of the specimen to finish
+// sums all partials in a fixed order (each thread a strided share, then
+// warp shuffles, then the warps in order) and advances the specimen's
+// control block:
 //   MODE_STEP, phase RUN:     sample (K, U, T) into the series, step count + 1,
 //                             burst over after nsteps samples
 //   MODE_STEP, phase REFRESH: forces refreshed and the first step started
@@ -42,9 +43,10 @@ __device__ __forceinline__ T lane_sum(T v) {
 template <int NT>
 __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double pe_w, double rr_w,
                                  double d2_w, double dp2_w, int mode, int phase, long long done,
-                                 long long nsteps, double (*red)[NT]) {
+                                 long long nsteps) {
     constexpr int NV = 5;  // K, U, R, max displacement^2 since the build and since the pruning
-    __shared__ double shw[NV][NT / 32];
+    constexpr int NW = NT / 32;
+    __shared__ double shw[NV][NW];
     __shared__ int is_last;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -57,7 +59,7 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
     __syncthreads();
     if (threadIdx.x == 0) {
         double k = 0, p = 0, r = 0, d = 0, e = 0;
-        for (int i = 0; i < NT / 32; ++i) {
+        for (int i = 0; i < NW; ++i) {
             k = k + shw[0][i];
             p = p + shw[1][i];
             r = r + shw[2][i];
@@ -86,36 +88,30 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
         v[3] = fmax(v[3], __ldcg(P + 3));
         v[4] = fmax(v[4], __ldcg(P + 4));
     }
-    for (int q = 0; q < NV; ++q) red[q][threadIdx.x] = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = v[0] + __shfl_xor_sync(0xffffffffu, v[0], o);
+        v[1] = v[1] + __shfl_xor_sync(0xffffffffu, v[1], o);
+        v[2] = v[2] + __shfl_xor_sync(0xffffffffu, v[2], o);
+        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+    }
+    __syncthreads();  // every warp has read shw above
+    if (lane == 0)
+        for (int q = 0; q < NV; ++q) shw[q][w] = v[q];
     __syncthreads();
-    // pairwise tree over the largest power of two P <= NT, after folding the
-    // NT - P top entries onto the first ones
-    constexpr int P = (NT & (NT - 1)) == 0 ? NT : (NT >= 256 && NT < 512 ? 256 : 0);
-    static_assert(P > 0, "block size");
-    if (P < NT) {
-        if (threadIdx.x < NT - P) {
-            red[0][threadIdx.x] = red[0][threadIdx.x] + red[0][threadIdx.x + P];
-            red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + P];
-            red[2][threadIdx.x] = red[2][threadIdx.x] + red[2][threadIdx.x + P];
-            red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + P]);
-            red[4][threadIdx.x] = fmax(red[4][threadIdx.x], red[4][threadIdx.x + P]);
+    double tot[NV] = {0, 0, 0, 0, 0};
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NW; ++i) {
+            tot[0] = tot[0] + shw[0][i];
+            tot[1] = tot[1] + shw[1][i];
+            tot[2] = tot[2] + shw[2][i];
+            tot[3] = fmax(tot[3], shw[3][i]);
+            tot[4] = fmax(tot[4], shw[4][i]);
         }
-        __syncthreads();
-    }
-    for (int s = P / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            red[0][threadIdx.x] = red[0][threadIdx.x] + red[0][threadIdx.x + s];
-            red[1][threadIdx.x] = red[1][threadIdx.x] + red[1][threadIdx.x + s];
-            red[2][threadIdx.x] = red[2][threadIdx.x] + red[2][threadIdx.x + s];
-            red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
-            red[4][threadIdx.x] = fmax(red[4][threadIdx.x], red[4][threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
     if (threadIdx.x != 0) return;
     SpecCtl *c = S.ctl;
-    const double K = red[0][0], U = red[1][0], T = red[2][0] * S.t_fac, md2 = red[3][0],
-                 mp2 = red[4][0];
+    const double K = tot[0], U = tot[1], T = tot[2] * S.t_fac, md2 = tot[3], mp2 = tot[4];
     if (mode == MODE_EVAL) {
         c->eval_obs[0] = K;
         c->eval_obs[1] = U;

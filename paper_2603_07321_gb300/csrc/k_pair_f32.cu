@@ -406,9 +406,8 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
     rr = warp_sum(rr);
     d2 = warp_max(d2);
     dp2 = warp_max(dp2);
-    __shared__ double red[5][TPB];
     step_tail<TPB>(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode, phase,
-                   done, nsteps, red);
+                   done, nsteps);
 }
 
 // Inner list: every lane keeps, in order, the entries of its own column of
@@ -630,9 +629,8 @@ __global__ void __launch_bounds__(TILE_T, 3) k_force_tile(const SpecDev *__restr
     rr = warp_sum(rr);
     d2 = warp_max(d2);
     dp2 = warp_max(dp2);
-    __syncthreads();  // the stage is reused as reduction scratch
     step_tail<TILE_T>(S, lb, (double)ke, (double)pe, (double)rr, (double)d2, (double)dp2, mode,
-                      phase, done, nsteps, reinterpret_cast<double (*)[TILE_T]>(stg));
+                      phase, done, nsteps);
 }
 
 // pruning of a tile's lists: the same test and order as k_prune_f32<1, 1>,
@@ -680,7 +678,6 @@ __global__ void __launch_bounds__(TILE_T, 3) k_prune_tile(const SpecDev *__restr
 }
 
 static constexpr size_t TILE_SMEM = (size_t)TILE_SC * sizeof(float4);
-static_assert(TILE_SMEM >= 5 * TILE_T * sizeof(double), "stage too small for the reduction");
 
 // opt the tile kernels into the dynamic shared memory they use (once)
 int tile_kernels_init() {
