@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
 }
 
 template <int L, int G, bool SC76>
-__global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict__ specs,
+__global__ void __launch_bounds__(TPB, G == 1 ? 9 : 8) k_force_f32(const SpecDev *__restrict__ specs,
                                                       const int *__restrict__ b2s, int mode) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     SpecCtl *ctl = S.ctl;
