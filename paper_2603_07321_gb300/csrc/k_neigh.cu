@@ -515,6 +515,36 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                         mixed ? nl_entry(0, 2 * (xx - cx[0]), 2 * (yy - cy[0]), 2 * (zz - cz[0])) -
                                     (unsigned)sub0
                               : nl_entry(0, xx - cx[0], yy - cy[0], zz - cz[0]);
+                    if (mixed && S.G == 1) {
+                        // one atom: the candidate test on the cell-relative records
+                        // (as in the one-lane path), the FP64 test for the thin band
+                        const float4 *__restrict__ crec = (const float4 *)S.posfp;
+                        const float4 ra = crec[a0];
+                        const float h = S.f_h;
+                        const float ox = ra.x - (float)(xx - cx[0]) * h,
+                                    oy = ra.y - (float)(yy - cy[0]) * h,
+                                    oz = ra.z - (float)(zz - cz[0]) * h;
+                        for (int j = s; j < e; ++j) {
+                            const float4 rj = crec[j];
+                            const float fx = rj.x - ox, fy = rj.y - oy, fz = rj.z - oz;
+                            const float r2f = fx * fx + fy * fy + fz * fz;
+                            bool in;
+                            if (r2f < S.f_rl2_lo)
+                                in = true;
+                            else if (r2f >= S.f_rl2_hi)
+                                in = false;
+                            else
+                                in = in_list(S, par, true, a0, x[0], y[0], z[0], ha[0], la[0], j);
+                            if (in && j != a0) {
+                                if (cnt < S.cap_use)
+                                    S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
+                                        (int)(((unsigned)j << NL_CODE_BITS) + code +
+                                              (unsigned)__float_as_int(rj.w));
+                                ++cnt;
+                            }
+                        }
+                        continue;
+                    }
                     for (int j = s; j < e; ++j) {
                         bool in = false;
                         for (int g = 0; g < ga && !in; ++g)
