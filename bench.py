@@ -48,13 +48,13 @@ WORKLOADS = {
                   desc="10^3-cell FCC Al cube (4,000 atoms), 300 K, tension 1e-3/s, "
                        "3 bursts x 2,000 steps per coarse step, FP64 throughout"),
     "batched": dict(name="batched_64x_n20", n_cells=20, T0=None, rate=None, burst=2000,
-                    precision=1, count=64,
+                    precision=1, count=64, lanes=1,
                     desc="64 replicas of a 20^3-cell cube (32,000 atoms each), T0 cycling "
                          "10/100/300 K, half tension half compression, rates log-uniform "
                          "1e-4..1e-3/s, 3 bursts x 2,000 steps per coarse step, one launch "
                          "set per fine step for all replicas"),
     "served": dict(name="served_poisson_16req", n_cells=None, T0=None, rate=None, burst=2000,
-                   precision=1, count=16,
+                   precision=1, count=16, lanes=1,
                    desc="first 16 requests of a Poisson trace (mean 2/s): cube side uniform "
                         "10..49 cells, T0 in 10/100/300 K, rate log-uniform 1e-4..1e-3/s, "
                         "tension or compression p=0.5, target strain 0.05..0.15, admitted by "
@@ -64,7 +64,7 @@ WORKLOADS = {
                       precision=1, count=7,
                       desc="mixed precision vs FP64 per size (10..49 cells), same seed"),
     "uneven": dict(name="uneven_28x_n10_49", n_cells=None, T0=300.0, rate=None, burst=2000,
-                   precision=1, count=28,
+                   precision=1, count=28, lanes=1,
                    desc="4 cubes each of 10,15,20,25,30,40,49 cells (3,786,384 atoms), "
                         "alternating tension/compression, 300 K, 3 bursts x 2,000 steps"),
 }
@@ -90,6 +90,14 @@ def captured_traffic(kernel: str, workload: str):
     except (OSError, KeyError, ValueError):
         return None
 N_SM = 152
+
+
+def lanes_of(args, wl) -> int:
+    """Threads per atom for the workload's specimens: --lanes if given, else
+    the workload's setting (batched workloads run one lane per atom: the
+    library's automatic choice sizes lanes for a specimen running alone, and a
+    batch fills the device without them), else 0 (automatic)."""
+    return args.lanes if args.lanes is not None else wl.get("lanes", 0)
 
 
 def perfect_lattice_pairs(n_cells: int, rc_over_a0: float = 2.0) -> int:
@@ -230,7 +238,8 @@ def run_served(args, wl):
     trace = PI.served_trace(16, seed=7 + rank)
     reqs = [Request(rid=i, n_cells=r.n_cells, T0=r.T0, seed=r.seed, strain_rate=r.strain_rate,
                     target_strain=r.target_strain, arrival_s=r.arrival_s,
-                    burst_steps=r.burst_steps, precision=wl["precision"])
+                    burst_steps=r.burst_steps, precision=wl["precision"],
+                    lanes=lanes_of(args, wl))
             for i, r in enumerate(trace)]
     eng = GPUEngine()
     free, _ = torch.cuda.mem_get_info()
@@ -267,7 +276,8 @@ def run_served(args, wl):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic (seeded Poisson request trace)",
                "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
-                          "live_specimens": len(sched.live), "parallelism": "continuous batching"},
+                          "live_specimens": len(sched.live), "parallelism": "continuous batching",
+                          "lanes_per_atom": lanes_of(args, wl) or "automatic"},
                "served": {"coarse_step_latency_s": {"p50": tick,
                                                     "p99": float(np.percentile(lat, 99))
                                                     if lat else None},
@@ -336,7 +346,8 @@ def run_pta(args, wl):
     ctxs = []
     for r in reqs:
         ctxs.append(P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=wl["precision"],
-                          burst_steps=r.burst_steps, strain_rate=r.strain_rate))
+                          burst_steps=r.burst_steps, strain_rate=r.strain_rate,
+                          lanes=lanes_of(args, wl)))
     natoms = sum(c.n for c in ctxs)
     batch = P.Batch(ctxs) if len(ctxs) > 1 else None
     stepper = batch if batch is not None else ctxs[0]
@@ -447,6 +458,7 @@ def run_pta(args, wl):
             "data": "synthetic (FCC lattice + seeded Maxwell-Boltzmann velocities)",
             "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
                        "specimens": len(ctxs), "fine_steps_per_step": fine_per_step,
+                       "lanes_per_atom": sorted({c.layout()["lanes"] for c in ctxs}),
                        "accumulators": "f64", "l2": "working set > 129 MB L2 (no flush)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "k_%s_f32" % dominant[0]
@@ -543,6 +555,9 @@ def main():
     ap.add_argument("--impl", default="pta", choices=["pta", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--lanes", type=int, default=None,
+                    help="threads per atom of every specimen (default: the workload's choice; "
+                         "0 = the library's per-specimen choice)")
     ap.add_argument("--prec-steps", type=int, default=1000,
                     help="burst length of the precision comparison")
     ap.add_argument("--ref-sample", type=int, default=4,

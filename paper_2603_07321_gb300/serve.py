@@ -33,6 +33,7 @@ class Request:
     arrival_s: float = 0.0
     burst_steps: int = 2000
     precision: int = 1
+    lanes: int = 0        # threads per atom (0: the library's per-specimen choice)
 
 
 @dataclass
@@ -210,7 +211,7 @@ class GPUEngine:
 
     def _p(self, req):
         return self._params(precision=req.precision, burst_steps=req.burst_steps,
-                            strain_rate=req.strain_rate)
+                            strain_rate=req.strain_rate, lanes=req.lanes)
 
     def footprint(self, req: Request) -> int:
         return int(self._fp(self._spec(req.n_cells), self._p(req)))
