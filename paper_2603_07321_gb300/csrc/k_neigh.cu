@@ -244,26 +244,30 @@ __global__ void k_scatter(const SpecDev *__restrict__ specs, const int *__restri
     S.cell_tmp[slot] = a;
 }
 
-// one warp per cell: order the cell's atoms by creation index (rank = number
-// of smaller ones), so that the order within a cell, and with it every list
-// order, does not depend on how cells are numbered; then clear the cell's
-// counter for the next build
+// each warp orders CELLS_PER_WARP cells in turn (most cells of the grid's
+// margin are empty): a cell's atoms by creation index (rank = number of
+// smaller ones), so that the order within a cell, and with it every list
+// order, does not depend on how cells are numbered; then the cell's counter
+// is cleared for the next build
 __global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
                             int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     if (!build_active(S, force)) return;
-    const int c = (blockIdx.x - S.blk_cell0) * CELL_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (c >= S.ncell) return;
-    const int s = S.cell_start[c], e = S.cell_start[c + 1];
-    for (int p = s + lane; p < e; p += 32) {
-        const int v = S.cell_tmp[p];
-        const int ov = S.orig[v];
-        int r = 0;
-        for (int q = s; q < e; ++q) r += (S.orig[S.cell_tmp[q]] < ov);
-        S.cell_atoms[s + r] = v;
+    const int c0 = (blockIdx.x - S.blk_cell0) * CELL_WARPS * CELLS_PER_WARP + (threadIdx.x >> 5);
+    for (int i = 0; i < CELLS_PER_WARP; ++i) {
+        const int c = c0 + i * CELL_WARPS;
+        if (c >= S.ncell) return;
+        const int s = S.cell_start[c], e = S.cell_start[c + 1];
+        for (int p = s + lane; p < e; p += 32) {
+            const int v = S.cell_tmp[p];
+            const int ov = S.orig[v];
+            int r = 0;
+            for (int q = s; q < e; ++q) r += (S.orig[S.cell_tmp[q]] < ov);
+            S.cell_atoms[s + r] = v;
+        }
+        if (lane == 0) S.cell_cnt[c] = 0;
     }
-    if (lane == 0) S.cell_cnt[c] = 0;
 }
 
 // sort the per-atom state into cell order: gather into scratch, then copy back

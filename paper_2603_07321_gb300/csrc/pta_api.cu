@@ -325,7 +325,7 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     if (ncell > (1LL << 30)) return PTA_EINVAL;
     z->ncell = (int)ncell;
     z->ntile_grid = (int)(ncell / 8);
-    z->nblk_cell = (z->ncell + CELL_WARPS - 1) / CELL_WARPS;
+    z->nblk_cell = (z->ncell + CELL_WARPS * CELLS_PER_WARP - 1) / (CELL_WARPS * CELLS_PER_WARP);
     // G = 2: at most one one-atom unit per cell besides the pairs
     if (z->G == 2) z->nunits = std::min<long long>(z->n, (z->n + 1) / 2 + z->ncell);
     z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);

@@ -17,6 +17,7 @@ namespace pta {
 
 constexpr int TPB = 128;        // threads per block of the atom and pair kernels
 constexpr int CELL_WARPS = 8;   // warps per block of the cell-sort kernel
+constexpr int CELLS_PER_WARP = 8;  // cells one warp of the cell-sort kernel orders in turn
 constexpr int SCAN_THREADS = 1024;
 
 // Cell tiles of the mixed-precision, one-lane-per-atom pair passes: a block
@@ -91,7 +92,7 @@ struct SpecDev {
                                // nunits is the capacity (units in use: SpecCtl::nunits)
     int blk_pair0, nblk_pair;  // pair kernels: TPB/L units per block
     int blk_atom0, nblk_atom;  // one thread per atom
-    int blk_cell0, nblk_cell;  // one warp per cell
+    int blk_cell0, nblk_cell;  // cell sort: CELLS_PER_WARP cells per warp
     int spec_index;            // index of this specimen in the launch table
     int tiled;                 // pair passes by cell tiles (nblk_pair blocks loop over them)
     int ntile_grid;            // tiles of the cell grid (ncell / 8)
