@@ -180,7 +180,7 @@ const char *pta_strerror(int status);
 int pta_abi_version(void);
 
 /* Defaults: Table 1 values (dt 1 fs, Delta = h/5 with h = 1 s, tolerances),
- * Al mass, skin 1 A, 2,000-step bursts, blocks of 100 steps, FP64. */
+ * Al mass, skin 2 A, 2,000-step bursts, blocks of 100 steps, FP64. */
 int pta_default_params(pta_params *out);
 /* Sutton-Chen Al (eps 3.3147e-2 eV, n 7, m 6, a 4.05 A), rc = 2 a, and c
  * chosen so that the perfect crystal under the cut potential is in

@@ -916,7 +916,7 @@ int pta_default_params(pta_params *p) {
     std::memset(p, 0, sizeof(*p));
     p->dt_fs = 1.0;
     p->mass_amu = 26.9815385;
-    p->skin = 1.0;
+    p->skin = 2.0;
     p->h = 1.0;
     p->Delta = 0.2;
     p->strain_rate = 1e-3;

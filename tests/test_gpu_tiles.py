@@ -4,7 +4,8 @@ A tile's atoms sum their neighbour lists in the same order and with the same
 arithmetic whether the neighbour records come from the tile's shared-memory
 copy, from global memory (a halo too dense for the copy), or from the
 untiled kernels: forces, energies and trajectories are identical bit for
-bit, and the neighbour sets equal the oracle's brute-force pairs.
+bit, and the neighbour sets equal the oracle's brute-force pairs.  The tiles'
+shared-memory copy is sized for a 1 A Verlet skin, which these tests use.
 """
 import numpy as np
 import pytest
@@ -13,6 +14,7 @@ import pta_inputs as PI
 from gpu_util import force_error_atom, gpu_package, on_grid, sorted_rows
 
 pytestmark = pytest.mark.gpu
+SKIN = 1.0
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +28,7 @@ def _pot(oracle, ctx):
 
 
 def _forces(P, shape, pos, tiles, a0=4.05):
-    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=1, cell_tiles=tiles, a0=a0)
+    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=1, cell_tiles=tiles, a0=a0, skin=SKIN)
     ctx.set_state(pos, np.zeros_like(pos))
     f, pe, obs = ctx.forces()
     info = ctx.tiling()
@@ -67,7 +69,7 @@ def test_tiled_trajectory_identical_to_untiled(P, oracle):
     out = []
     for tiles in (1, -1):
         ctx = P.Ctx((9, 8, 10), T0=300.0, seed=21, precision=P.PREC_MIXED, lanes=1,
-                    cell_tiles=tiles)
+                    cell_tiles=tiles, skin=SKIN)
         ctx.apply_strain(2e-3)
         a = ctx.fine_burst(300)
         out.append((ctx.series().copy(), ctx.get_state(), a.prunes, a.rebuilds))
@@ -81,7 +83,7 @@ def test_tiled_trajectory_identical_to_untiled(P, oracle):
 
 @pytest.mark.parametrize("shape", [(5, 4, 6), (7, 7, 7)])
 def test_tiled_neighbour_sets_bit_exact(P, oracle, shape):
-    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=P.PREC_MIXED, cell_tiles=1)
+    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=P.PREC_MIXED, cell_tiles=1, skin=SKIN)
     assert ctx.layout()["lanes"] == 1 and ctx.tiling()["tiled"]
     pos = on_grid(PI.jittered_fcc(shape, 0.35, seed=sum(shape) + 40))
     ctx.set_state(pos, np.zeros_like(pos))
@@ -100,7 +102,7 @@ def test_more_occupied_tiles_than_blocks(P, oracle):
     pos = on_grid(2.0 * PI.gaussian_jitter_fcc(shape, 0.05, seed=33))
     res = []
     for tiles in (1, -1):
-        ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=1, cell_tiles=tiles)
+        ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=1, cell_tiles=tiles, skin=SKIN)
         ctx.set_state(pos, np.zeros_like(pos))
         f, pe, _ = ctx.forces()
         res.append((f, pe, ctx.tiling()))
@@ -111,7 +113,8 @@ def test_more_occupied_tiles_than_blocks(P, oracle):
 
 
 def test_batch_of_tiled_and_untiled_specimens_equals_solo(P, oracle):
-    kw = [dict(cell_tiles=1, lanes=1), dict(cell_tiles=-1, lanes=2), dict(cell_tiles=1, lanes=1)]
+    kw = [dict(cell_tiles=1, lanes=1, skin=SKIN), dict(cell_tiles=-1, lanes=2, skin=SKIN),
+          dict(cell_tiles=1, lanes=1, skin=SKIN)]
     shapes = [(7, 7, 8), (6, 6, 7), (8, 6, 7)]
     solo = []
     for sh, k in zip(shapes, kw):
