@@ -22,6 +22,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                    reversibility, momentum, fixed grips)
 * coarse-step logic .............. pinned (linear and step sequences, truth
                                    table of the acceptance rules)
+* adaptive burst length .......... pinned (closed-form crossing of a linear
+                                   series, constant and alternating series,
+                                   floors, N_max, brute-force recomputation)
 """
 from __future__ import annotations
 

@@ -165,3 +165,61 @@ def run(specimen, params: PTAParams, burst_steps: int, n_coarse: int, block: int
         st, res = coarse_update(params, st, *Rs)
         out.append((specimen.u / specimen.L_s, res))
     return out, st
+
+
+# ---------------------------------------------------------------------------
+# Adaptive burst length (appendix, Eq. (R_m_conv))
+# ---------------------------------------------------------------------------
+def converged_averages(series, lag: int, tol, floor, n_max: int | None = None):
+    """The running-average convergence test of the appendix on a burst's
+    per-step samples (rows r = 1, 2, ... of `series`, columns K, U, T).
+
+    Running average R^(i) = (1/i) sum_{r<=i} m_r, summed in step order.  The
+    test e^m(i) = |R^(i) - R^(i-k)| / |R^(i)| < tol_m (Eq. (R_m_conv)) is
+    applied every k = `lag` steps, at i = 2k, 3k, ... (R^(i-k) needs i > k).
+    Readings where the appendix is silent (the CUDA path takes the same):
+    k is a parameter; the denominator is max(|R^(i)|, floor_m), as in the
+    coarse-step tests; each variable converges on its own (N_s^m = the first
+    passing i, R^m = R^(N_s^m)), and the burst ends once all three have
+    converged or after n_max samples, where an unconverged variable takes the
+    running average of all samples.
+
+    Returns (means, counts, converged_mask, steps_run).
+    """
+    s = np.asarray(series, dtype=np.float64)
+    n = len(s) if n_max is None else min(len(s), n_max)
+    sums = [0.0, 0.0, 0.0]
+    chk = [0.0, 0.0, 0.0]
+    conv_n = [0, 0, 0]
+    conv_v = [0.0, 0.0, 0.0]
+    mask = 0
+    run = n
+    for i in range(1, n + 1):
+        for q in range(3):
+            sums[q] = sums[q] + float(s[i - 1, q])
+        if i % lag == 0:
+            if i >= 2 * lag:
+                for q in range(3):
+                    if mask & (1 << q):
+                        continue
+                    a = sums[q] / float(i)
+                    b = chk[q] / float(i - lag)
+                    e = abs(a - b) / max(abs(a), floor[q])
+                    if e < tol[q]:
+                        mask |= 1 << q
+                        conv_n[q] = i
+                        conv_v[q] = a
+            for q in range(3):
+                chk[q] = sums[q]
+            if mask == 7:
+                run = i
+                break
+    means, counts = [], []
+    for q in range(3):
+        if mask & (1 << q):
+            means.append(conv_v[q])
+            counts.append(conv_n[q])
+        else:
+            means.append(sums[q] / float(run))
+            counts.append(run)
+    return np.array(means), np.array(counts), mask, run

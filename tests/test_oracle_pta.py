@@ -99,3 +99,92 @@ def test_protocol_increments_sum_to_rate_times_h():
     assert sum(p.step_increments()) == pytest.approx(-3e-4 * 1.0, rel=1e-15)
     assert sum(p.init_increments()) == pytest.approx(-3e-4 * p.Delta, rel=1e-15)
     assert p.Delta == pytest.approx(0.2)
+
+
+# ---------------------------------------------------------------------------
+# adaptive burst length: the appendix's running-average convergence test
+# ---------------------------------------------------------------------------
+def _linear(n, a, b):
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return a + b * i
+
+
+def test_convergence_of_linear_series_at_the_closed_form_step():
+    # m_i = a + b i has R^(i) = a + b (i + 1) / 2, so R^(i) - R^(i-k) = b k / 2 and
+    # e(i) = (b k / 2) / (a + b (i + 1) / 2) < tol  <=>  i > k / tol - 2 a / b - 1
+    from oracle.pta_logic import converged_averages
+    k = 10
+    cols = [(1.0, 1.0, 0.05), (100.0, 1.0, 0.05), (0.0, 1.0, 0.02)]
+    s = np.stack([_linear(2000, a, b) for a, b, _ in cols], axis=1)
+    tol = [t for _, _, t in cols]
+    means, counts, mask, run = converged_averages(s, k, tol, (1e-12, 1e-12, 1e-12))
+    expect = []
+    for a, b, t in cols:
+        bound = k / t - 2 * a / b - 1
+        i = 2 * k
+        while not i > bound:
+            i += k
+        expect.append(i)
+    assert list(counts) == expect == [200, 20, 500]
+    assert mask == 7 and run == 500
+    for q, (a, b, _) in enumerate(cols):
+        assert means[q] == pytest.approx(a + b * (expect[q] + 1) / 2, rel=1e-14)
+
+
+def test_constant_and_periodic_series_converge_at_the_first_test():
+    from oracle.pta_logic import converged_averages
+    n, k = 400, 8
+    i = np.arange(1, n + 1)
+    s = np.stack([np.full(n, 3.5), 7.0 + 0.5 * (-1.0) ** i, -2.0 + np.cos(np.pi * i / 2)], axis=1)
+    means, counts, mask, run = converged_averages(s, k, (1e-9,) * 3, (1e-12,) * 3)
+    # k a multiple of the periods: R^(2k) = R^(k) exactly, e = 0
+    assert mask == 7 and run == 2 * k and list(counts) == [2 * k] * 3
+    assert np.allclose(means, [3.5, 7.0, -2.0], rtol=0, atol=1e-14)
+
+
+def test_zero_tolerance_runs_to_n_max_with_the_full_average():
+    from oracle.pta_logic import converged_averages
+    rng = np.random.default_rng(3)
+    s = 1.0 + rng.normal(0, 0.1, (300, 3))
+    means, counts, mask, run = converged_averages(s, 10, (0.0,) * 3, (1e-12,) * 3, n_max=250)
+    assert mask == 0 and run == 250 and list(counts) == [250] * 3
+    assert np.allclose(means, s[:250].mean(axis=0), rtol=1e-13)
+
+
+def test_floor_lets_a_near_zero_stress_converge():
+    from oracle.pta_logic import converged_averages
+    n, k = 2000, 7
+    i = np.arange(1, n + 1)
+    t = 1e-3 * (-1.0) ** i                 # a stress that averages to 0 GPa
+    s = np.stack([np.full(n, 5.0), np.full(n, -9.0), t], axis=1)
+    # with the 0.05 GPa floor: e(14) = |0 - (-1e-3 / 7)| / 0.05 < 0.05
+    _, counts, mask, _ = converged_averages(s, k, (0.05,) * 3, (1e-12, 1e-12, 0.05))
+    assert mask == 7 and counts[2] == 2 * k
+    # relative to the running average itself (0 at even i, -1e-3 / i at odd
+    # i, for an odd lag) e is 1 or unbounded: it never converges
+    _, counts, mask, run = converged_averages(s, k, (0.05,) * 3, (1e-12, 1e-12, 1e-300))
+    assert not mask & 4 and run == n and counts[2] == n
+
+
+def test_convergence_against_brute_force_recomputation():
+    from oracle.pta_logic import converged_averages
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        n, k = int(rng.integers(50, 600)), int(rng.integers(1, 40))
+        s = rng.normal([10.0, -50.0, 0.2], [1.0, 0.5, 0.3], (n, 3))
+        tol = rng.uniform(0.001, 0.05, 3)
+        means, counts, mask, run = converged_averages(s, k, tol, (1e-12, 1e-12, 0.05))
+        # brute force: every candidate step checked from scratch
+        for q in range(3):
+            first = None
+            for i in range(2 * k, n + 1, k):
+                a = s[:i, q].sum() / i
+                b = s[:i - k, q].sum() / (i - k)
+                if abs(a - b) / max(abs(a), (1e-12, 1e-12, 0.05)[q]) < tol[q]:
+                    first = i
+                    break
+            if first is not None and first <= run:
+                assert mask & (1 << q) and counts[q] == first
+                assert means[q] == pytest.approx(s[:first, q].mean(), rel=1e-12, abs=1e-12)
+            else:
+                assert not mask & (1 << q) and counts[q] == run
