@@ -132,21 +132,36 @@ typedef struct {
                            lane count 1; PTA_EUNSUPPORTED for FP64,
                            atoms_per_thread 2 or lanes > 1); 0 (default) and
                            -1 = off                                          */
+    int conv_lag;       /* adaptive burst length (appendix, Eq. (R_m_conv)):
+                           every conv_lag steps from 2 conv_lag on, variable m
+                           has converged once |R^(i) - R^(i-k)| /
+                           max(|R^(i)|, floor[m]) < conv_tol[m], R^ the running
+                           average; the burst ends when all three have, or at
+                           its length (N_max).  0 (default) = fixed length   */
+    double conv_tol[3]; /* tol_m of the convergence test (Table 1: 5% each)    */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
  * full step (the initial state is not sampled), standard errors from
  * non-overlapping blocks of block_steps samples (NaN with fewer than two
  * blocks), the number of neighbour-list builds and inner-list prunings
- * during the burst. */
+ * during the burst.  With an adaptive burst length (pta_params.conv_lag > 0,
+ * appendix, Eq. (R_m_conv)) the burst stops once every variable's running
+ * average has converged: mean[m] is then the running average at that
+ * variable's own convergence step nsamples[m] (bit `m` of `converged` set),
+ * se[m] comes from the blocks within those samples, and nsteps is the
+ * number of steps run; a variable that has not converged when the burst
+ * reaches its length keeps the average of all samples.  Without it,
+ * nsamples[m] = nsteps and converged = 0. */
 typedef struct {
     double mean[3];
     double se[3];
     int64_t nsteps;
     int32_t rebuilds;
-    int32_t status; /* pta_status of this burst */
-    int32_t prunes; /* inner-list prunings during the burst (mixed precision) */
-    int32_t pad;
+    int32_t status;    /* pta_status of this burst */
+    int32_t prunes;    /* inner-list prunings during the burst (mixed precision) */
+    int32_t converged; /* adaptive length: bit m set when variable m converged */
+    int64_t nsamples[3];
 } pta_averages;
 
 /* Coarse step t -> t+h.  v_pred: Eq. (pta_pred); v_d: Eq. (simp); e_v:

@@ -69,17 +69,20 @@ class Params(ctypes.Structure):
                 ("burst_steps", ctypes.c_int64), ("block_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("neigh_cap", ctypes.c_int),
                 ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
-                ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int)]
+                ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int),
+                ("conv_lag", ctypes.c_int), ("conv_tol", ctypes.c_double * 3)]
 
 
 class Averages(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double * 3), ("se", ctypes.c_double * 3),
                 ("nsteps", ctypes.c_int64), ("rebuilds", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("prunes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("prunes", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("nsamples", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {"mean": list(self.mean), "se": list(self.se), "nsteps": self.nsteps,
-                "rebuilds": self.rebuilds, "prunes": self.prunes, "status": self.status}
+                "rebuilds": self.rebuilds, "prunes": self.prunes, "status": self.status,
+                "converged": self.converged, "nsamples": list(self.nsamples)}
 
 
 class CoarseResult(ctypes.Structure):
@@ -217,7 +220,7 @@ def default_params(**kw) -> Params:
     p = Params()
     _check(load().pta_default_params(ctypes.byref(p)), "pta_default_params")
     for k, v in kw.items():
-        if k in ("tol_v", "tol_j", "floor"):
+        if k in ("tol_v", "tol_j", "floor", "conv_tol"):
             for i in range(3):
                 getattr(p, k)[i] = v[i]
         else:

@@ -132,6 +132,26 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
                 c->sum[2] = c->sum[2] + T;
                 c->done = done + 1;
                 if (done + 1 >= nsteps) c->phase = PH_IDLE;
+                const long long i = done + 1;
+                if (S.conv_lag > 0 && i % S.conv_lag == 0) {
+                    // appendix, Eq. (R_m_conv): e = |R^(i) - R^(i-k)| / max(|R^(i)|,
+                    // floor), from i = 2k on; each variable converges on its own
+                    if (i >= 2LL * S.conv_lag) {
+                        for (int q = 0; q < 3; ++q) {
+                            if (c->conv_mask & (1 << q)) continue;
+                            const double a = c->sum[q] / (double)i;
+                            const double b = c->sum_chk[q] / (double)(i - S.conv_lag);
+                            const double e = fabs(a - b) / fmax(fabs(a), S.floor_[q]);
+                            if (e < S.conv_tol[q]) {
+                                c->conv_mask |= 1 << q;
+                                c->conv_n[q] = i;
+                                c->conv_val[q] = a;
+                            }
+                        }
+                        if (c->conv_mask == 7) c->phase = PH_IDLE;
+                    }
+                    for (int q = 0; q < 3; ++q) c->sum_chk[q] = c->sum[q];
+                }
             }
         } else if (phase == PH_REFRESH) {
             c->phase = PH_RUN;

@@ -302,6 +302,12 @@ __global__ void k_burst_begin(const SpecDev *__restrict__ specs, const long long
     c->nsteps = n;
     c->done = 0;
     c->sum[0] = c->sum[1] = c->sum[2] = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        c->sum_chk[q] = 0.0;
+        c->conv_val[q] = 0.0;
+        c->conv_n[q] = 0;
+    }
+    c->conv_mask = 0;
     c->rebuilds = 0;
     c->prunes = 0;
     c->blocks_done = 0;
@@ -322,13 +328,21 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
     __shared__ double sh[TPB];
     const long long n = c->done;
     const int B = S.block_steps > 0 ? S.block_steps : 100;
-    const long long nb = n / B;
+    const bool adaptive = S.conv_lag > 0;
     double mean[3], bmean[3], se[3];
+    long long nq[3];
     for (int q = 0; q < 3; ++q) {
+        // adaptive length: a converged variable reports the running average
+        // at its convergence step, the others the running average of all
+        // samples (both from the step-ordered running sums)
+        const bool conv = adaptive && (c->conv_mask & (1 << q));
+        nq[q] = conv ? c->conv_n[q] : n;
+        const long long nb = nq[q] / B;
         double s = 0;
         for (long long i = threadIdx.x; i < n; i += TPB) s = s + S.series[3 * i + q];
         s = block_sum<TPB>(s, sh);
         mean[q] = (n > 0) ? s / (double)n : nan("");
+        if (adaptive && n > 0) mean[q] = conv ? c->conv_val[q] : c->sum[q] / (double)n;
         // block means and their mean
         double sb = 0;
         for (long long b = threadIdx.x; b < nb; b += TPB) {
@@ -357,7 +371,8 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
         r.nsteps = n;
         r.rebuilds = c->rebuilds;
         r.prunes = c->prunes;
-        r.pad = 0;
+        r.converged = adaptive ? c->conv_mask : 0;
+        for (int q = 0; q < 3; ++q) r.nsamples[q] = nq[q];
         int e = c->err;
         r.status = (e & ERR_OVERFLOW) ? PTA_ENEIGH_OVERFLOW
                    : (e & ERR_NAN)    ? PTA_ENAN
@@ -368,6 +383,18 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
             for (int q = 0; q < 3; ++q) c->pta.R3[slot][q] = mean[q];
         out[blockIdx.x] = r;
     }
+}
+
+// adaptive burst lengths: is any specimen of the table still in its burst?
+__global__ void k_any_running(const SpecDev *__restrict__ specs, int nspec, int *flag) {
+    int run = 0;
+    for (int s = threadIdx.x; s < nspec; s += blockDim.x) run |= specs[s].ctl->phase != PH_IDLE;
+    run = __syncthreads_or(run);
+    if (threadIdx.x == 0) *flag = run;
+}
+
+void launch_any_running(const Tab &t, int *flag, cudaStream_t st) {
+    k_any_running<<<1, 128, 0, st>>>(t.specs, t.nspec, flag);
 }
 
 void launch_burst_end(const Tab &t, int slot, pta_averages *out, cudaStream_t st) {

@@ -421,6 +421,9 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
                                  (par->lanes != 0 && par->lanes != 1)))
         return PTA_EUNSUPPORTED;
     if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
+    if (par->conv_lag < 0) return PTA_EINVAL;
+    for (int q = 0; q < 3; ++q)
+        if (!(par->conv_tol[q] >= 0) || !std::isfinite(par->conv_tol[q])) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
     if (n > (long long)MAX_ATOMS) return PTA_ERANGE;
     if (par->precision == PTA_PREC_MIXED) {
@@ -769,18 +772,38 @@ static int run_burst(Runner *r, const int64_t *nsteps, pta_averages *out, int sl
     CK(cudaMemcpyAsync(r->d_nsteps, r->h_nsteps, 8 * k, cudaMemcpyHostToDevice, r->stream));
     launch_burst_begin(r->tab, r->d_nsteps, r->stream);
     CKR(launch_check());
+    // adaptive burst lengths end on the device: after every chunk the host
+    // asks whether any member is still running (d_ops/h_ops[0] serve as the
+    // flag; the coarse-step update copies its own ops later)
+    bool adaptive = false;
+    for (int i = 0; i < k; ++i) adaptive |= r->m[i]->par.conv_lag > 0;
+    auto still_running = [&](bool &run) -> int {
+        run = true;
+        if (!adaptive) return PTA_OK;
+        launch_any_running(r->tab, r->d_ops, r->stream);
+        CKR(launch_check());
+        CK(cudaMemcpyAsync(r->h_ops, r->d_ops, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
+        CK(cudaStreamSynchronize(r->stream));
+        run = r->h_ops[0] != 0;
+        return PTA_OK;
+    };
+    bool run = true;
     if (r->timing) {
-        for (long long q = 0; q < iters / CHUNK; ++q) {
+        for (long long q = 0; q < iters / CHUNK && run; ++q) {
             CK(cudaGraphLaunch(r->t_chunk, r->stream));
             CKR(collect_times(r, CHUNK));
+            CKR(still_running(run));
         }
-        for (long long q = 0; q < iters % CHUNK; ++q) {
+        for (long long q = 0; q < iters % CHUNK && run; ++q) {
             CK(cudaGraphLaunch(r->t_one, r->stream));
             CKR(collect_times(r, 1));
         }
     } else {
-        for (long long q = 0; q < iters / CHUNK; ++q) CK(cudaGraphLaunch(r->g_chunk, r->stream));
-        for (long long q = 0; q < iters % CHUNK; ++q) CK(cudaGraphLaunch(r->g_one, r->stream));
+        for (long long q = 0; q < iters / CHUNK && run; ++q) {
+            CK(cudaGraphLaunch(r->g_chunk, r->stream));
+            CKR(still_running(run));
+        }
+        for (long long q = 0; q < iters % CHUNK && run; ++q) CK(cudaGraphLaunch(r->g_one, r->stream));
     }
     launch_burst_end(r->tab, slot, r->d_avg, r->stream);
     CKR(launch_check());
@@ -935,6 +958,8 @@ int pta_default_params(pta_params *p) {
     p->neigh_cap = 0;
     p->lanes = 0;
     p->cell_tiles = 0;
+    p->conv_lag = 0;
+    p->conv_tol[0] = p->conv_tol[1] = p->conv_tol[2] = 0.05;
     return PTA_OK;
 }
 
@@ -1103,7 +1128,9 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
         s.tol_v[q] = c->par.tol_v[q];
         s.tol_j[q] = c->par.tol_j[q];
         s.floor_[q] = c->par.floor[q];
+        s.conv_tol[q] = c->par.conv_tol[q];
     }
+    s.conv_lag = c->par.conv_lag;
     s.series_cap = z.series_cap;
     c->L_s = c->spec.n_cells[s.axis] * c->spec.a0;
     rc = ctx_alloc_all(c, z);

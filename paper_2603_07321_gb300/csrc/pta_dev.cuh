@@ -77,7 +77,12 @@ struct SpecCtl {
     int prune;                 // 1: prune the inner list before the next pair pass
     int prunes;                // prunings in the current burst
     int ntiles;                // occupied cell tiles at the last build
-    double sum[3];             // running sums of K, U, T over the burst
+    double sum[3];             // running sums of K, U, T over the burst (in step order)
+    double sum_chk[3];         // adaptive length: running sums at the last check
+    double conv_val[3];        // adaptive length: running average at convergence
+    long long conv_n[3];       // adaptive length: step of convergence per variable
+    int conv_mask;             // adaptive length: bit m set once variable m converged
+    int conv_pad;
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
     pta_averages last;         // averages of the last finished burst
@@ -116,6 +121,9 @@ struct SpecDev {
     int block_steps;
     // coarse-step constants (Table 1)
     double pta_h, pta_Delta, tol_v[3], tol_j[3], floor_[3];
+    // adaptive burst length (appendix): test every conv_lag steps (0 = off)
+    int conv_lag;
+    double conv_tol[3];
     // arrays
     void *pos[2];   // FP64: double4 {x,y,z,0};  MIXED: float4 hi {x,y,z,0}
     float4 *lo[2];  // MIXED only: float4 lo {x,y,z,0}
@@ -349,6 +357,7 @@ void launch_export(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_strain(const Tab &t, const double *du, cudaStream_t st);
 void launch_burst_begin(const Tab &t, const long long *nsteps, cudaStream_t st);
 void launch_burst_end(const Tab &t, int slot, pta_averages *out, cudaStream_t st);
+void launch_any_running(const Tab &t, int *flag, cudaStream_t st);
 void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
 void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
 void launch_rebuild(const Tab &t, int force, cudaStream_t st);
