@@ -22,6 +22,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                    reversibility, momentum, fixed grips)
 * coarse-step logic .............. pinned (linear and step sequences, truth
                                    table of the acceptance rules)
+* mean positions (Eq. mean_pos) .. pinned (free atoms in closed form, fixed
+                                   grips, one-step burst)
 * adaptive burst length .......... pinned (closed-form crossing of a linear
                                    series, constant and alternating series,
                                    floors, N_max, brute-force recomputation)
@@ -319,6 +321,19 @@ class Specimen:
             raise ValueError("neighbour capacity exceeded")
         self.last_forces = f
         return series
+
+    def burst_mean_positions(self, nsteps: int, cap: int = 512):
+        """Eq. (mean_pos): run nsteps of velocity Verlet and return the series
+        and the mean position of every atom over the states sampled after each
+        full step, (1/N) sum_i r(sigma_i), summed in FP64 in step order.  The
+        steps run one at a time (each call starts from the forces of its
+        starting positions, exactly those the previous step ended with)."""
+        series = np.zeros((nsteps, 3))
+        acc = np.zeros((self.n, 3))
+        for s in range(nsteps):
+            series[s] = self.burst(1, cap)[0]
+            acc = acc + self.pos
+        return series, acc / nsteps
 
     def observables(self, cap: int = 512):
         out = np.zeros(3)

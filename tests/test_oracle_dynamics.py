@@ -127,3 +127,43 @@ def test_burst_averages_block_se(oracle):
     assert np.allclose(mean, x.mean(axis=0))
     # iid data: block SE ~ sigma / sqrt(N)
     assert np.all(np.abs(se / (2.0 / np.sqrt(4000)) - 1) < 0.35)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (mean_pos): mean atomic positions over a burst's sampled states
+# ---------------------------------------------------------------------------
+def test_mean_positions_of_free_atoms_in_closed_form(oracle):
+    # two atoms farther apart than rc feel no force: r_i = r_0 + v dt i, so
+    # the mean over i = 1..N is r_0 + v dt (N + 1) / 2
+    spec = oracle.Specimen((4, 4, 4))
+    spec.pos = np.array([[0.0, 0.0, 0.0], [30.0, 1.0, -2.0]])
+    spec.vel = np.array([[1e-3, 2e-3, 0.0], [0.0, 0.0, -1e-3]])
+    spec.flags = np.zeros(2, dtype=np.uint8)
+    r0, v = spec.pos.copy(), spec.vel.copy()
+    n = 37
+    series, mean = spec.burst_mean_positions(n)
+    assert np.allclose(mean, r0 + v * spec.dt * (n + 1) / 2, rtol=0, atol=1e-13)
+    assert np.allclose(spec.pos, r0 + v * spec.dt * n, rtol=0, atol=1e-13)
+
+
+def test_mean_positions_keep_grips_and_follow_the_trajectory(oracle):
+    a = oracle.Specimen((5, 5, 6))
+    a.thermalise(300.0, 9)
+    a.apply_strain(1e-3)
+    b = oracle.Specimen((5, 5, 6))
+    b.pos, b.vel, b.u = a.pos.copy(), a.vel.copy(), a.u
+    grips = a.flags != 0
+    p0 = a.pos.copy()
+    series, mean = a.burst_mean_positions(20)
+    # grip atoms do not move: their mean is their position (up to the
+    # rounding of summing 20 equal values)
+    assert np.array_equal(a.pos[grips], p0[grips])
+    assert np.allclose(mean[grips], p0[grips], rtol=0, atol=1e-12)
+    # the step-by-step run is the same trajectory as one 20-step burst
+    s_ref = b.burst(20)
+    assert np.array_equal(series, s_ref) and np.array_equal(a.pos, b.pos)
+    # one-step burst: the mean is the state after that step
+    c = oracle.Specimen((5, 5, 6))
+    c.pos, c.vel = p0.copy(), a.vel.copy()
+    _, m1 = c.burst_mean_positions(1)
+    assert np.array_equal(m1, c.pos)
