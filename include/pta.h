@@ -139,6 +139,9 @@ typedef struct {
                            average; the burst ends when all three have, or at
                            its length (N_max).  0 (default) = fixed length   */
     double conv_tol[3]; /* tol_m of the convergence test (Table 1: 5% each)    */
+    int mean_positions; /* 1: also average every atom's position over the
+                           states a burst samples (Eq. (mean_pos)), read with
+                           pta_get_mean_positions; 0 (default) = off        */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
@@ -242,6 +245,11 @@ int pta_get_strain(const pta_ctx *ctx, double *strain);
  * (which the next burst continues from, Eqs. (x_guess_step1),
  * (x_guess_step3)).  Blocks until the averages are on the host.  nsteps >= 1. */
 int pta_fine_burst(pta_ctx *ctx, int64_t nsteps, pta_averages *out);
+/* Eq. (mean_pos): every atom's mean position over the states the last
+ * burst sampled (after each full step), n x 3 doubles in creation order, A.
+ * Needs pta_params.mean_positions = 1 (else PTA_EUNSUPPORTED) and a burst
+ * with at least one sample (else PTA_EINVAL); n must equal the atom count. */
+int pta_get_mean_positions(pta_ctx *ctx, double *out, int64_t n);
 /* The K, U, T samples of the last burst, nsteps x 3 doubles; *count gets
  * the number of samples (at most max_steps are copied). */
 int pta_get_series(pta_ctx *ctx, double *series, int64_t max_steps, int64_t *count);

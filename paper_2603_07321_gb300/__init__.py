@@ -70,7 +70,8 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("neigh_cap", ctypes.c_int),
                 ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
                 ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int),
-                ("conv_lag", ctypes.c_int), ("conv_tol", ctypes.c_double * 3)]
+                ("conv_lag", ctypes.c_int), ("conv_tol", ctypes.c_double * 3),
+                ("mean_positions", ctypes.c_int)]
 
 
 class Averages(ctypes.Structure):
@@ -124,6 +125,7 @@ _SIGS = {
     "pta_natoms": (ctypes.c_int, [_VP, _P(ctypes.c_int64)]),
     "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_tiling": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
+    "pta_get_mean_positions": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64]),
     "pta_get_flags": (ctypes.c_int, [_VP, _P(ctypes.c_uint8), ctypes.c_int64]),
     "pta_apply_strain": (ctypes.c_int, [_VP, ctypes.c_double]),
     "pta_get_strain": (ctypes.c_int, [_VP, _P(ctypes.c_double)]),
@@ -287,6 +289,12 @@ def pta_get_tiling(h) -> dict:
     out = (ctypes.c_int32 * 4)()
     _check(load().pta_get_tiling(h, out), "pta_get_tiling")
     return {"tiled": bool(out[0]), "blocks": out[1], "tiles": out[2], "staged_tiles": out[3]}
+
+
+def pta_get_mean_positions(h, n):
+    out = np.zeros((n, 3))
+    _check(load().pta_get_mean_positions(h, _dptr(out), n), "pta_get_mean_positions")
+    return out
 
 
 def pta_get_flags(h, n):
@@ -482,6 +490,9 @@ class Ctx:
 
     def tiling(self):
         return pta_get_tiling(self.h)
+
+    def mean_positions(self):
+        return pta_get_mean_positions(self.h, self.n)
 
     def apply_strain(self, d_eps):
         pta_apply_strain(self.h, d_eps)

@@ -229,6 +229,13 @@ __device__ __forceinline__ void atom_update(const SpecDev &S, SpecCtl *ctl, int 
     }
     const float4 hia = ((const float4 *)S.pos[par])[a];
     const float4 loa = S.lo[par][a];
+    if (phase == PH_RUN && S.rsum) {
+        // Eq. (mean_pos): the sampled state's position, hi + lo exactly
+        double *rs = S.rsum + 4LL * S.orig[a];
+        rs[0] = rs[0] + ((double)hia.x + (double)loa.x);
+        rs[1] = rs[1] + ((double)hia.y + (double)loa.y);
+        rs[2] = rs[2] + ((double)hia.z + (double)loa.z);
+    }
     float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
     const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
     if (start && flag == FLAG_MOBILE) {

@@ -110,6 +110,13 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
                     v.z += fz * kh;
                 }
                 ke = S.ke_fac * ((v.x * v.x + v.y * v.y) + v.z * v.z);
+                if (S.rsum) {
+                    // Eq. (mean_pos): the sampled state's position
+                    double *rs = S.rsum + 4LL * S.orig[a];
+                    rs[0] = rs[0] + pa.x;
+                    rs[1] = rs[1] + pa.y;
+                    rs[2] = rs[2] + pa.z;
+                }
             }
             double x = pa.x, y = pa.y, z = pa.z;
             const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);

@@ -248,7 +248,7 @@ static PotDev make_pot(const pta_potential &p) {
 struct Sizes {
     long long n, nunits;
     int L, G, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
-    int prune_on, tiled, ntile_grid;
+    int prune_on, tiled, ntile_grid, mean_pos;
     double prune_margin;
     double h, org[3];
     size_t list_words;
@@ -286,6 +286,7 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     // lower occupancy, so they measured slower on the 470,596-atom cube
     z->tiled = (par.precision == PTA_PREC_MIXED && z->G == 1 && z->L == 1 && par.cell_tiles == 1)
                    ? 1 : 0;
+    z->mean_pos = par.mean_positions ? 1 : 0;
     const double rl = p.rc + par.skin;
     z->prune_margin = par.prune_margin == 0.0 ? 0.3 : par.prune_margin;
     z->prune_on = (par.precision == PTA_PREC_MIXED && z->prune_margin > 0.0 &&
@@ -390,6 +391,7 @@ static size_t footprint(const Sizes &z, int prec) {
     add(64 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
+    if (z.mean_pos) add(32 * n);     // rsum
     add(48 * n);                     // stage
     add(sizeof(SpecCtl));
     add(sizeof(SpecDev));
@@ -422,6 +424,7 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
         return PTA_EUNSUPPORTED;
     if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
     if (par->conv_lag < 0) return PTA_EINVAL;
+    if (par->mean_positions != 0 && par->mean_positions != 1) return PTA_EINVAL;
     for (int q = 0; q < 3; ++q)
         if (!(par->conv_tol[q] >= 0) || !std::isfinite(par->conv_tol[q])) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
@@ -770,6 +773,9 @@ static int run_burst(Runner *r, const int64_t *nsteps, pta_averages *out, int sl
         if (nsteps[i] > 0) iters = std::max<long long>(iters, nsteps[i] + 1);
     }
     CK(cudaMemcpyAsync(r->d_nsteps, r->h_nsteps, 8 * k, cudaMemcpyHostToDevice, r->stream));
+    for (int i = 0; i < k; ++i)  // mean positions start from zero with every burst
+        if (nsteps[i] > 0 && r->m[i]->hd.rsum)
+            CK(cudaMemsetAsync(r->m[i]->hd.rsum, 0, 32 * (size_t)r->m[i]->hd.n, r->stream));
     launch_burst_begin(r->tab, r->d_nsteps, r->stream);
     CKR(launch_check());
     // adaptive burst lengths end on the device: after every chunk the host
@@ -959,6 +965,7 @@ int pta_default_params(pta_params *p) {
     p->lanes = 0;
     p->cell_tiles = 0;
     p->conv_lag = 0;
+    p->mean_positions = 0;
     p->conv_tol[0] = p->conv_tol[1] = p->conv_tol[2] = 0.05;
     return PTA_OK;
 }
@@ -1032,6 +1039,9 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     AL(part, 64 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
+    if (z.mean_pos) {
+        AL(rsum, 32 * n, double *);
+    }
     AL(stage, 48 * n, double *);
     AL(ctl, sizeof(SpecCtl), SpecCtl *);
 #undef AL
@@ -1212,6 +1222,22 @@ int pta_get_tiling(pta_ctx *c, int32_t out[4]) {
     out[2] = ctl.ntiles;
     for (int k = 0; k < ctl.ntiles && k < (int)list.size(); ++k)
         out[3] += tab[(size_t)list[k] * TT_STRIDE + TT_STAGED] != 0;
+    return PTA_OK;
+}
+
+int pta_get_mean_positions(pta_ctx *c, double *out, int64_t n) {
+    if (!c || !out || n != c->hd.n) return PTA_EINVAL;
+    if (!c->hd.rsum) return PTA_EUNSUPPORTED;
+    if (c->broken) return PTA_ECUDA;
+    std::vector<double> buf(4 * (size_t)n);
+    SpecCtl ctl;
+    CK(cudaMemcpyAsync(buf.data(), c->hd.rsum, 32 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&ctl, c->hd.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (ctl.done < 1) return PTA_EINVAL;
+    const double inv = (double)ctl.done;
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) out[3 * i + d] = buf[4 * (size_t)i + d] / inv;
     return PTA_OK;
 }
 

@@ -151,6 +151,8 @@ struct SpecDev {
     double *series;     // series_cap x 3 samples of the current burst
     long long series_cap;
     double *eval_out;   // n x 4: F, pe (MODE_EVAL)
+    double *rsum;       // n x 4, creation order: sums of the sampled positions of the
+                        // burst (Eq. (mean_pos)); null unless asked for
     double *stage;      // n x 6 doubles: import/export staging
     SpecCtl *ctl;
 };
