@@ -24,6 +24,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                    table of the acceptance rules)
 * mean positions (Eq. mean_pos) .. pinned (free atoms in closed form, fixed
                                    grips, one-step burst)
+* thermal relaxation burst ....... pinned (transverse grip coordinates and
+                                   left grip unchanged, energy conservation,
+                                   the unrelaxed reaction relaxes)
 * adaptive burst length .......... pinned (closed-form crossing of a linear
                                    series, constant and alternating series,
                                    floors, N_max, brute-force recomputation)
@@ -100,6 +103,9 @@ def _load():
         "or_burst": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_long, ctypes.c_int, dp, dp]),
+        "or_burst_relax": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_long, ctypes.c_int, dp, dp]),
         "or_observables": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]),
     }
@@ -307,12 +313,14 @@ class Specimen:
                                 _ptr(self.flags, ctypes.c_uint8), self.axis, du)
         self.u += du
 
-    def burst(self, nsteps: int, cap: int = 512):
+    def burst(self, nsteps: int, cap: int = 512, relax: bool = False):
         """Run nsteps of velocity Verlet; returns the series [nsteps, 3] of
-        (K eV, U eV, T GPa) sampled after every full step."""
+        (K eV, U eV, T GPa) sampled after every full step.  relax: the right
+        grip moves freely along the load axis (thermal relaxation)."""
         series = np.zeros((nsteps, 3))
         f = np.zeros((self.n, 3))
-        rc = _load().or_burst(_ptr(self.pos, ctypes.c_double), _ptr(self.vel, ctypes.c_double),
+        fn = _load().or_burst_relax if relax else _load().or_burst
+        rc = fn(_ptr(self.pos, ctypes.c_double), _ptr(self.vel, ctypes.c_double),
                               self.n, _ptr(self.flags, ctypes.c_uint8),
                               ctypes.byref(self.pot._c()), self.mass, self.dt, self.axis,
                               self.A0, nsteps, cap, _ptr(series, ctypes.c_double),

@@ -614,10 +614,15 @@ OR_API void or_apply_strain(double *pos, long n, const uint8_t *flags, int axis,
  * running time average of Eq. (R_m_t) is the mean of the series.
  * Pairs are found again from scratch at every step.  Returns 0, or -1 when
  * an atom has more than `cap` neighbours.
+ *
+ * With right_free (thermal relaxation, Sec. Boundary conditions) the
+ * right-grip atoms move freely along the load axis: that component of their
+ * velocity and force enters the update like a mobile atom's, the other two
+ * stay v = 0, F = 0.  The left grip stays fixed.
  * ------------------------------------------------------------------- */
-OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
-                    double mass, double dt, int axis, double A0, long nsteps, int cap,
-                    double *series, double *f_out) {
+static int burst_impl(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
+                      double mass, double dt, int axis, double A0, long nsteps, int cap,
+                      double *series, double *f_out, int right_free) {
     or_work w;
     w.cap = cap;
     w.counts = (int *)malloc(sizeof(int) * n);
@@ -629,8 +634,9 @@ OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, cons
     const double acc = or_force_to_acc() / mass;
     for (long s = 0; s < nsteps && rc == 0; s++) {
         for (long i = 0; i < n; i++) {
-            if (flags[i] != 0) continue;
             for (int d = 0; d < 3; d++) {
+                const int moves = flags[i] == 0 || (right_free && flags[i] == 2 && d == axis);
+                if (!moves) continue;
                 vel[3 * i + d] = vel[3 * i + d] + w.f[3 * i + d] * acc * (0.5 * dt);
                 pos[3 * i + d] = pos[3 * i + d] + vel[3 * i + d] * dt;
             }
@@ -638,9 +644,10 @@ OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, cons
         rc = or_forces(pos, n, p, &w);
         if (rc != 0) break;
         for (long i = 0; i < n; i++) {
-            if (flags[i] != 0) continue;
-            for (int d = 0; d < 3; d++)
-                vel[3 * i + d] = vel[3 * i + d] + w.f[3 * i + d] * acc * (0.5 * dt);
+            for (int d = 0; d < 3; d++) {
+                const int moves = flags[i] == 0 || (right_free && flags[i] == 2 && d == axis);
+                if (moves) vel[3 * i + d] = vel[3 * i + d] + w.f[3 * i + d] * acc * (0.5 * dt);
+            }
         }
         if (series) or_observe(n, vel, w.f, w.pe, flags, mass, axis, A0, series + 3 * s);
     }
@@ -651,6 +658,19 @@ OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, cons
     free(w.pe);
     free(w.rho);
     return rc;
+}
+
+OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
+                    double mass, double dt, int axis, double A0, long nsteps, int cap,
+                    double *series, double *f_out) {
+    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 0);
+}
+
+/* the same burst with the right grip free along the load axis (relaxation) */
+OR_API int or_burst_relax(double *pos, double *vel, long n, const uint8_t *flags,
+                          const or_pot *p, double mass, double dt, int axis, double A0,
+                          long nsteps, int cap, double *series, double *f_out) {
+    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 1);
 }
 
 /* state functions of a given state (no time step) */
