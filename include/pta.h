@@ -245,6 +245,19 @@ int pta_get_strain(const pta_ctx *ctx, double *strain);
  * (which the next burst continues from, Eqs. (x_guess_step1),
  * (x_guess_step3)).  Blocks until the averages are on the host.  nsteps >= 1. */
 int pta_fine_burst(pta_ctx *ctx, int64_t nsteps, pta_averages *out);
+/* Thermal relaxation before loading (Sec. Boundary conditions): bursts of
+ * `window` steps with the right grip free to move along the load axis (its
+ * other velocity components stay 0; the left grip stays fixed) until the
+ * window mean of T is within tol_gpa of 0, or until another window would
+ * exceed max_steps.  The right-grip atoms are then fixed where the
+ * relaxation left them (v = 0), and later grip displacements count from
+ * there.  *out gets the
+ * last window's averages, *steps the steps run (either may be NULL).
+ * NVE has no damping: the free grip oscillates about the stress-free
+ * position, so windows of many oscillation periods (thousands of steps)
+ * judge it.  window >= 1, max_steps >= window, tol_gpa >= 0. */
+int pta_relax(pta_ctx *ctx, int64_t window, int64_t max_steps, double tol_gpa,
+              pta_averages *out, int64_t *steps);
 /* Eq. (mean_pos): every atom's mean position over the states the last
  * burst sampled (after each full step), n x 3 doubles in creation order, A.
  * Needs pta_params.mean_positions = 1 (else PTA_EUNSUPPORTED) and a burst

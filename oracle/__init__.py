@@ -330,6 +330,20 @@ class Specimen:
         self.last_forces = f
         return series
 
+    def relax(self, window: int, max_steps: int, tol_gpa: float, cap: int = 512):
+        """Thermal relaxation (Sec. Boundary conditions): relaxation bursts of
+        `window` steps until the window mean of T is within tol_gpa of 0 or
+        another window would exceed max_steps; then the right grip is fixed
+        where it is (v = 0).  Returns (last window's series, steps run)."""
+        total = 0
+        while True:
+            s = self.burst(window, cap, relax=True)
+            total += window
+            if abs(s[:, 2].mean()) < tol_gpa or total + window > max_steps:
+                break
+        self.vel[self.flags == 2] = 0.0
+        return s, total
+
     def burst_mean_positions(self, nsteps: int, cap: int = 512):
         """Eq. (mean_pos): run nsteps of velocity Verlet and return the series
         and the mean position of every atom over the states sampled after each

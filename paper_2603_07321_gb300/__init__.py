@@ -126,6 +126,8 @@ _SIGS = {
     "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_tiling": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_mean_positions": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64]),
+    "pta_relax": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                 _P(Averages), _P(ctypes.c_int64)]),
     "pta_get_flags": (ctypes.c_int, [_VP, _P(ctypes.c_uint8), ctypes.c_int64]),
     "pta_apply_strain": (ctypes.c_int, [_VP, ctypes.c_double]),
     "pta_get_strain": (ctypes.c_int, [_VP, _P(ctypes.c_double)]),
@@ -289,6 +291,14 @@ def pta_get_tiling(h) -> dict:
     out = (ctypes.c_int32 * 4)()
     _check(load().pta_get_tiling(h, out), "pta_get_tiling")
     return {"tiled": bool(out[0]), "blocks": out[1], "tiles": out[2], "staged_tiles": out[3]}
+
+
+def pta_relax(h, window: int, max_steps: int, tol_gpa: float):
+    a = Averages()
+    steps = ctypes.c_int64()
+    _check(load().pta_relax(h, int(window), int(max_steps), float(tol_gpa), ctypes.byref(a),
+                            ctypes.byref(steps)), "pta_relax")
+    return a, steps.value
 
 
 def pta_get_mean_positions(h, n):
@@ -493,6 +503,9 @@ class Ctx:
 
     def mean_positions(self):
         return pta_get_mean_positions(self.h, self.n)
+
+    def relax(self, window=2000, max_steps=50000, tol_gpa=0.05):
+        return pta_relax(self.h, window, max_steps, tol_gpa)
 
     def apply_strain(self, d_eps):
         pta_apply_strain(self.h, d_eps)

@@ -219,11 +219,18 @@ __device__ __forceinline__ void atom_update(const SpecDev &S, SpecCtl *ctl, int 
         return;
     }
     const float kh = S.f_acc_half;
+    // thermal relaxation: the right grip moves along the load axis only (its
+    // other velocity components stay 0, so the drift leaves them in place)
+    const bool rfree = flag == FLAG_RIGHT && ctl->relax;
     if (phase == PH_RUN) {
         if (flag == FLAG_MOBILE) {
             v.x += fx * kh;
             v.y += fy * kh;
             v.z += fz * kh;
+        } else if (rfree) {
+            if (S.axis == 0) v.x += fx * kh;
+            else if (S.axis == 1) v.y += fy * kh;
+            else v.z += fz * kh;
         }
         ke += S.f_ke_fac * (v.x * v.x + v.y * v.y + v.z * v.z);
     }
@@ -238,10 +245,18 @@ __device__ __forceinline__ void atom_update(const SpecDev &S, SpecCtl *ctl, int 
     }
     float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
     const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
-    if (start && flag == FLAG_MOBILE) {
-        v.x += fx * kh;
-        v.y += fy * kh;
-        v.z += fz * kh;
+    if (start && (flag == FLAG_MOBILE || rfree)) {
+        if (flag == FLAG_MOBILE) {
+            v.x += fx * kh;
+            v.y += fy * kh;
+            v.z += fz * kh;
+        } else if (S.axis == 0) {
+            v.x += fx * kh;
+        } else if (S.axis == 1) {
+            v.y += fy * kh;
+        } else {
+            v.z += fz * kh;
+        }
         const float dt = S.f_dt;
         qq[0] += v.x * dt;
         qq[1] += v.y * dt;

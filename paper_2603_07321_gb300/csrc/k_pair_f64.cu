@@ -103,11 +103,17 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
             ((double4_32a *)S.eval_out)[S.orig[a]] = make_double4_32a(fx, fy, fz, pe);
         } else {
             const double kh = S.acc_half;
+            // thermal relaxation: the right grip moves along the load axis only
+            const bool rfree = flag == FLAG_RIGHT && S.ctl->relax;
             if (phase == PH_RUN) {
                 if (flag == FLAG_MOBILE) {
                     v.x += fx * kh;
                     v.y += fy * kh;
                     v.z += fz * kh;
+                } else if (rfree) {
+                    if (S.axis == 0) v.x += fx * kh;
+                    else if (S.axis == 1) v.y += fy * kh;
+                    else v.z += fz * kh;
                 }
                 ke = S.ke_fac * ((v.x * v.x + v.y * v.y) + v.z * v.z);
                 if (S.rsum) {
@@ -120,10 +126,18 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
             }
             double x = pa.x, y = pa.y, z = pa.z;
             const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
-            if (start && flag == FLAG_MOBILE) {
-                v.x += fx * kh;
-                v.y += fy * kh;
-                v.z += fz * kh;
+            if (start && (flag == FLAG_MOBILE || rfree)) {
+                if (flag == FLAG_MOBILE) {
+                    v.x += fx * kh;
+                    v.y += fy * kh;
+                    v.z += fz * kh;
+                } else if (S.axis == 0) {
+                    v.x += fx * kh;
+                } else if (S.axis == 1) {
+                    v.y += fy * kh;
+                } else {
+                    v.z += fz * kh;
+                }
                 x += v.x * S.dt;
                 y += v.y * S.dt;
                 z += v.z * S.dt;

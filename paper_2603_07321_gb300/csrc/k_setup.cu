@@ -254,6 +254,21 @@ __global__ void k_export(const SpecDev *__restrict__ sp) {
     }
 }
 
+// end of thermal relaxation: the right grip is fixed where it is, v = 0
+__global__ void k_fix_right_grip(const SpecDev *__restrict__ sp) {
+    const SpecDev &S = *sp;
+    const int a = blockIdx.x * TPB + threadIdx.x;
+    if (a >= S.n || S.flags[a] != FLAG_RIGHT) return;
+    if (S.prec == PTA_PREC_FP64)
+        ((double4_32a *)S.vel)[a] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    else
+        ((float4 *)S.vel)[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+void launch_fix_right_grip(const SpecDev &h, const SpecDev *d, cudaStream_t st) {
+    k_fix_right_grip<<<(h.n + TPB - 1) / TPB, TPB, 0, st>>>(d);
+}
+
 void launch_import(const SpecDev &h, const SpecDev *d, cudaStream_t st) {
     k_import<<<(h.n + TPB - 1) / TPB, TPB, 0, st>>>(d);
 }

@@ -1225,6 +1225,32 @@ int pta_get_tiling(pta_ctx *c, int32_t out[4]) {
     return PTA_OK;
 }
 
+int pta_relax(pta_ctx *c, int64_t window, int64_t max_steps, double tol_gpa, pta_averages *out,
+              int64_t *steps) {
+    if (!c || window < 1 || max_steps < window || !(tol_gpa >= 0)) return PTA_EINVAL;
+    Runner *r;
+    CKR(ctx_solo(c, &r));
+    const int on = 1, off = 0;
+    CK(cudaMemcpyAsync(&c->hd.ctl->relax, &on, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    int64_t total = 0;
+    pta_averages a{};
+    int rc = PTA_OK;
+    while (rc == PTA_OK) {
+        rc = run_burst(r, &window, &a, -1);
+        if (rc != PTA_OK) break;
+        total += a.nsteps;
+        if (std::fabs(a.mean[2]) < tol_gpa || total + window > max_steps) break;
+    }
+    CK(cudaMemcpyAsync(&c->hd.ctl->relax, &off, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    launch_fix_right_grip(c->hd, c->d_self, c->stream);
+    CKR(launch_check());
+    CK(cudaStreamSynchronize(c->stream));
+    if (rc == PTA_ECUDA) c->broken = true;
+    if (out) *out = a;
+    if (steps) *steps = total;
+    return rc;
+}
+
 int pta_get_mean_positions(pta_ctx *c, double *out, int64_t n) {
     if (!c || !out || n != c->hd.n) return PTA_EINVAL;
     if (!c->hd.rsum) return PTA_EUNSUPPORTED;

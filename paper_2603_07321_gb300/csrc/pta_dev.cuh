@@ -82,7 +82,7 @@ struct SpecCtl {
     double conv_val[3];        // adaptive length: running average at convergence
     long long conv_n[3];       // adaptive length: step of convergence per variable
     int conv_mask;             // adaptive length: bit m set once variable m converged
-    int conv_pad;
+    int relax;                 // 1: thermal relaxation, right grip free along the load axis
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
     pta_averages last;         // averages of the last finished burst
@@ -355,6 +355,7 @@ void launch_create(const SpecDev &h, const SpecDev *d, double sigma_v, double kT
                    cudaStream_t st);
 void launch_import(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_export(const SpecDev &h, const SpecDev *d, cudaStream_t st);
+void launch_fix_right_grip(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 // batched
 void launch_strain(const Tab &t, const double *du, cudaStream_t st);
 void launch_burst_begin(const Tab &t, const long long *nsteps, cudaStream_t st);

@@ -207,3 +207,12 @@ def test_relaxation_relieves_the_reaction_of_the_unrelaxed_cube(oracle):
     T_free = free.burst(3000, relax=True)[:, 2].mean()
     assert abs(T_fixed) > 0.5
     assert abs(T_free) < 0.1 * abs(T_fixed)
+
+
+def test_relaxation_procedure_stops_at_the_tolerance_and_fixes_the_grip(oracle):
+    spec = oracle.Specimen(4)
+    s, steps = spec.relax(500, 5000, tol_gpa=1e9)     # any mean passes: one window
+    assert steps == 500 and np.all(spec.vel[spec.flags == 2] == 0)
+    spec = oracle.Specimen(4)
+    s, steps = spec.relax(500, 1600, tol_gpa=0.0)     # nothing passes: three windows
+    assert steps == 1500
