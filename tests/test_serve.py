@@ -144,3 +144,26 @@ def test_latency_statistics():
     assert st["coarse_step_latency_s"]["count"] > 0
     assert st["curve_latency_s"]["p50"] <= st["curve_latency_s"]["p99"]
     assert st["atom_steps"] > 0
+
+
+def test_request_lanes_and_precision_reach_the_engine_parameters():
+    # the parameters a request is created with depend on the request alone,
+    # so its results are the same alone and in any mix
+    from paper_2603_07321_gb300.serve import GPUEngine, Request
+    eng = GPUEngine()
+    r = Request(rid=1, n_cells=12, T0=300.0, seed=3, strain_rate=-2e-4, target_strain=0.05,
+                burst_steps=500, precision=1, lanes=1)
+    p = eng._p(r)
+    assert (p.lanes, p.precision, p.burst_steps, p.strain_rate) == (1, 1, 500, -2e-4)
+    assert eng._p(Request(rid=2, n_cells=12, T0=300.0, seed=3, strain_rate=1e-3,
+                          target_strain=0.05)).lanes == 0
+    assert eng.footprint(r) > 0
+
+
+def test_bench_lanes_follow_the_workload_unless_overridden():
+    import argparse
+    import bench
+    wl = bench.WORKLOADS["batched"]
+    assert bench.lanes_of(argparse.Namespace(lanes=None), wl) == 1
+    assert bench.lanes_of(argparse.Namespace(lanes=0), wl) == 0
+    assert bench.lanes_of(argparse.Namespace(lanes=None), bench.WORKLOADS["large"]) == 0
