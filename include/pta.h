@@ -254,8 +254,8 @@ int pta_fine_burst(pta_ctx *ctx, int64_t nsteps, pta_averages *out);
  * there.  *out gets the
  * last window's averages, *steps the steps run (either may be NULL).
  * NVE has no damping: the free grip oscillates about the stress-free
- * position, so windows of many oscillation periods (thousands of steps)
- * judge it.  window >= 1, max_steps >= window, tol_gpa >= 0. */
+ * position, so the window must span many oscillation periods (thousands of
+ * steps).  window >= 1, max_steps >= window, tol_gpa >= 0. */
 int pta_relax(pta_ctx *ctx, int64_t window, int64_t max_steps, double tol_gpa,
               pta_averages *out, int64_t *steps);
 /* Eq. (mean_pos): every atom's mean position over the states the last

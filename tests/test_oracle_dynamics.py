@@ -200,7 +200,7 @@ def test_relaxation_relieves_the_reaction_of_the_unrelaxed_cube(oracle):
     # the cube cut from the bulk lattice pulls on its fixed grips; with the
     # right grip free the time-averaged reaction falls to a small fraction
     # (NVE has no damping: the free grip oscillates about the stress-free
-    # position, so the reaction is judged by its mean over many periods)
+    # position, so the reaction is compared by its mean over many periods)
     fixed = oracle.Specimen(5)
     T_fixed = fixed.burst(3000)[:, 2].mean()
     free = oracle.Specimen(5)
