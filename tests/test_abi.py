@@ -143,3 +143,28 @@ def test_neighbour_list_layout_index():
         q = 2
         words = sorted(nl_index(a, q * L + l, L, cap) for a in range(G) for l in range(L))
         assert words == list(range(words[0], words[0] + 32))
+
+
+def test_new_parameters_are_validated_before_touching_the_gpu(P):
+    lib = P.load()
+    spec = P.make_specimen(4)
+    pot = P.default_potential()
+    h = ctypes.c_void_p()
+    bad = [dict(conv_lag=-1), dict(conv_tol=(0.05, float("nan"), 0.05)),
+           dict(conv_tol=(-0.1, 0.05, 0.05)), dict(mean_positions=2), dict(cell_tiles=2),
+           dict(precision=0, cell_tiles=1)]
+    for kw in bad:
+        par = P.default_params(**kw)
+        rc = lib.pta_create(ctypes.byref(spec), ctypes.byref(pot), 300.0, 1, ctypes.byref(par),
+                            None, ctypes.byref(h))
+        assert rc in (-1, -8), kw
+    par = P.default_params()
+    assert par.conv_lag == 0 and list(par.conv_tol) == [0.05] * 3
+    assert par.mean_positions == 0 and par.skin == 2.0
+    # the footprint grows by the mean-position sums when they are asked for
+    f0 = P.pta_footprint_bytes(spec, P.default_params(precision=1))
+    f1 = P.pta_footprint_bytes(spec, P.default_params(precision=1, mean_positions=1))
+    assert f1 - f0 >= 32 * 4 * 4 ** 3
+    # calls on a null context are rejected
+    assert lib.pta_relax(None, 10, 10, 0.0, None, None) == -1
+    assert lib.pta_get_mean_positions(None, None, 0) == -1
