@@ -68,10 +68,11 @@ __device__ __forceinline__ float rsqrt_nr(float r2) {
 // once; the second follows as d_1 = d_0 - (rel_1 - rel_0), which is exactly 0
 // for the entry that is the second atom itself (then skipped).
 //
-// The entry loop is unrolled by two; the next two entries are read before
-// the current two are evaluated.  Those reads go past a unit's count into
-// the four spare iterations every list keeps, whose entries are valid
-// indices, so the loop carries no bounds tests.
+// The entry loop is unrolled by two (by four in the one-atom density pass);
+// the next two (four) entries are read before the current ones are
+// evaluated.  Those reads go past a unit's count into the eight spare
+// iterations every list keeps, whose entries are valid indices, so the loop
+// carries no bounds tests.
 
 // the entries lane l of unit u reads (the inner list when pruning is on, else
 // the Verlet list), as a pointer to its first word (stride 32) and a count
@@ -322,6 +323,23 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             dg[1] = unit_dg(S, a0, ra[0], ra[1]);
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
+        if constexpr (G == 1 && SC76) {
+            unsigned e0 = __ldg(lst), e1 = __ldg(lst + 32), e2 = __ldg(lst + 64), e3 = __ldg(lst + 96);
+            for (int q = 0; q < cl; q += 4) {
+                const unsigned n0 = __ldg(lst + (q + 4) * 32), n1 = __ldg(lst + (q + 5) * 32);
+                const unsigned n2 = __ldg(lst + (q + 6) * 32), n3 = __ldg(lst + (q + 7) * 32);
+                const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
+                const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
+                float2 dx, dy, dz;
+                entry_disp2(e0, e1, x0, x1, ra[0], h, h8, h64, dx, dy, dz);
+                acc.add2(S, dx, dy, dz, q + 1 < cl);
+                if (q + 2 < cl) {
+                    entry_disp2(e2, e3, x2, x3, ra[0], h, h8, h64, dx, dy, dz);
+                    acc.add2(S, dx, dy, dz, q + 3 < cl);
+                }
+                e0 = n0; e1 = n1; e2 = n2; e3 = n3;
+            }
+        } else {
         unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
         for (int q = 0; q < cl; q += 2) {
             const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
@@ -337,6 +355,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             }
             ea = na;
             eb = nb;
+        }
         }
     }
 #pragma unroll
