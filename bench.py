@@ -8,7 +8,7 @@ FP64 accumulators) and the coarse-step update.  The metric is atom-steps/s
 (atoms x fine steps per second), whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pta|reference]
-                    [--workload large|plain|batched|uneven|served|precision]
+                    [--workload large|plain|batched|uneven|served|precision|profile]
 
 Under torchrun (N > 1) every rank advances its own specimen (independent
 replicas, no collective on the data path); the time is the maximum over
@@ -63,13 +63,17 @@ WORKLOADS = {
     "precision": dict(name="precision_by_size", n_cells=None, T0=300.0, rate=None, burst=1000,
                       precision=1, count=7,
                       desc="mixed precision vs FP64 per size (10..49 cells), same seed"),
+    "profile": dict(name="profile_case", n_cells=None, T0=300.0, rate=None, burst=None,
+                    precision=1, count=1,
+                    desc="one specimen for Nsight Compute captures: --n-cells cube, "
+                         "--precision, a 1e-3 strain step, a warm burst of --prof-warm steps "
+                         "and a burst of --prof-steps steps"),
     "uneven": dict(name="uneven_28x_n10_49", n_cells=None, T0=300.0, rate=None, burst=2000,
                    precision=1, count=28, lanes=1,
                    desc="4 cubes each of 10,15,20,25,30,40,49 cells (3,786,384 atoms), "
                         "alternating tension/compression, 300 K, 3 bursts x 2,000 steps"),
 }
 
-FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
 
 
 def captured_traffic(kernel: str, workload: str):
@@ -89,7 +93,21 @@ def captured_traffic(kernel: str, workload: str):
         return int(vals["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
-N_SM = 152
+
+
+def measure_fma_peaks(P, target_ms: float = 150.0):
+    """FMA rates of this GPU (TFLOP/s) from the library's probe: scalar FP32,
+    packed FP32 (two lanes per instruction) and FP64, each one launch of about
+    target_ms after a calibration launch."""
+    out = {}
+    for kind, name in ((0, "fp32"), (1, "fp32x2"), (2, "fp64")):
+        it = 2000 if kind < 2 else 200
+        P.pta_measure_fma_rate(kind, it)
+        fl, ms = P.pta_measure_fma_rate(kind, it)
+        it = max(it, int(it * target_ms / max(ms, 1e-3)))
+        fl, ms = P.pta_measure_fma_rate(kind, it)
+        out[name] = fl / (ms / 1e3) / 1e12
+    return out
 
 
 def lanes_of(args, wl) -> int:
@@ -332,6 +350,31 @@ def run_precision(args, wl):
     return out
 
 
+def run_profile(args, wl):
+    """A small, fixed case for profiler captures (run it under Nsight Compute
+    with PTA_GRAPH_FLAT=1, graphs without conditional nodes, whose kernel
+    nodes the profiler can capture); prints the second burst's throughput."""
+    import torch
+    import paper_2603_07321_gb300 as P
+    P.build()
+    torch.cuda.set_device(0)
+    ctx = P.Ctx(args.n_cells, T0=300.0, seed=1, precision=args.precision,
+                lanes=args.lanes or 0)
+    ctx.apply_strain(1e-3)
+    ctx.fine_burst(args.prof_warm)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    a = ctx.fine_burst(args.prof_steps)
+    dt = time.perf_counter() - t
+    out = {"workload": "profile_case", "n_cells": args.n_cells, "atoms": ctx.n,
+           "precision": args.precision, "steps": args.prof_steps, "seconds": dt,
+           "atom_steps_per_s": ctx.n * args.prof_steps / dt, "rebuilds": a.rebuilds,
+           "prunes": a.prunes, "layout": ctx.layout()}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return out
+
+
 def run_pta(args, wl):
     import torch
     import paper_2603_07321_gb300 as P
@@ -366,9 +409,15 @@ def run_pta(args, wl):
     for _ in range(args.warmup):
         one_step()
     barrier()
+    # the FP32 / FP64 FMA peaks of this GPU, measured with its clocks sampled
+    psampler = ClockSampler(local)
+    psampler.start()
+    peaks = measure_fma_peaks(P)
+    peak_clocks = psampler.stop()
+    barrier()
+    # headline: the coarse steps alone, no per-kernel timing events
     sampler = ClockSampler(local)
     sampler.start()
-    stepper.set_timing(True)
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -380,9 +429,19 @@ def run_pta(args, wl):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(ms, "cuda")
+    # per-kernel split, from a separate coarse step with CUDA events around
+    # each part of every fine-step iteration (reported apart from the headline)
+    stepper.set_timing(True)
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(st)
+    one_step()
+    e3.record(st)
+    barrier()
+    split_ms = e2.elapsed_time(e3)
     kt = stepper.timing()
     stepper.set_timing(False)
-    t_max = max_over_ranks(ms, "cuda")
     fine_per_step = 3 * max(r.burst_steps for r in reqs)
     atom_steps_rank = sum(c.n * 3 * r.burst_steps for c, r in zip(ctxs, reqs)) * args.steps
     value = atom_steps_rank * ws / (t_max / 1e3)
@@ -395,8 +454,9 @@ def run_pta(args, wl):
     dens_ms = kt.density_ms / iters
     flops_force = pairs * FLOP_FORCE_PAIR + natoms * (FLOP_ATOM - 5)
     flops_dens = pairs * FLOP_DENSITY_PAIR + natoms * 5
-    clk = clocks["sm_max_mhz"] or 2070.0
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # the peak: the larger measured FP32 FMA rate (scalar or packed)
+    peak_tflops = max(peaks["fp32"], peaks["fp32x2"])
     ach_force = flops_force / (force_ms / 1e3) / 1e12
     ach_dens = flops_dens / (dens_ms / 1e3) / 1e12
     dominant = ("force", ach_force, force_ms) if force_ms >= dens_ms else ("density", ach_dens,
@@ -467,11 +527,17 @@ def run_pta(args, wl):
                          "frac": dominant[1] / peak_tflops,
                          "traffic": captured_traffic("k_%s_f32" % dominant[0], wl["name"])
                          if wl["precision"] == 1 else None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz "
-                                        "(recipe unit counts, measured max clock)" % clk,
+                         "peak_source": "measured: FMA-chain probe (pta_measure_fma_rate) "
+                                        "on this GPU, %d SMs, median SM clock %s MHz; the "
+                                        "larger of scalar and packed FP32" % (
+                                            n_sm, peak_clocks["sm_mhz"]),
+                         "peaks_measured_tflops": peaks,
                          "launch_ms": dominant[2],
                          "kernels_ms_per_iteration": {"rebuild": kt.rebuild_ms / iters,
-                                                      "density": dens_ms, "force": force_ms}},
+                                                      "density": dens_ms, "force": force_ms},
+                         "split_run": "one extra coarse step with per-iteration CUDA events "
+                                      "(%d iterations, %.1f ms), not part of the headline" % (
+                                          kt.iterations, split_ms)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -562,6 +628,10 @@ def main():
                     help="burst length of the precision comparison")
     ap.add_argument("--ref-sample", type=int, default=4,
                     help="fine steps per reference-arm step")
+    ap.add_argument("--n-cells", type=int, default=49, help="profile workload: cube side")
+    ap.add_argument("--precision", type=int, default=1, help="profile workload: 0 FP64, 1 mixed")
+    ap.add_argument("--prof-warm", type=int, default=5, help="profile workload: warm burst")
+    ap.add_argument("--prof-steps", type=int, default=30, help="profile workload: timed burst")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -572,6 +642,8 @@ def main():
         run_served(args, wl)
     elif args.workload == "precision":
         run_precision(args, wl)
+    elif args.workload == "profile":
+        run_profile(args, wl)
     else:
         run_pta(args, wl)
 

@@ -274,6 +274,18 @@ int pta_get_series(pta_ctx *ctx, double *series, int64_t max_steps, int64_t *cou
  * -Delta, -Delta/2, 0, and sets v(0) to their Simpson value. */
 int pta_coarse_step(pta_ctx *ctx, pta_coarse_result *out);
 
+/* The coarse-step update alone, on three given burst results instead of
+ * three bursts: means[3 * b + m] is R^m of burst b (b = 0, 1, 2 at
+ * t+h-Delta, t+h-Delta/2, t+h; m = K, U, T).  The first call on a context
+ * whose initial bursts have not run treats them as the bursts labelled
+ * -Delta, -Delta/2, 0 and sets v(0) to their Simpson value, Eq. (simp); every
+ * later call is one update t -> t+h of Eqs. (dvdt_algo), (pta_pred), (simp),
+ * (rel_err), (jump_err), in the same kernel and on the same slow-variable
+ * record as pta_coarse_step.  No grip moves and no dynamics run.  For
+ * replaying the slow-time logic on recorded burst averages.  out->burst[b]
+ * carries the given means (nsteps 0).  PTA_EINVAL for non-finite means. */
+int pta_coarse_update(pta_ctx *ctx, const double means[9], pta_coarse_result *out);
+
 /* State exchange (host copies, n x 3 doubles each, library atom order).
  * pta_set_state replaces positions and velocities; grip atoms keep
  * whatever velocity is given (callers normally pass 0). */
@@ -315,7 +327,7 @@ int pta_get_timing(pta_ctx *ctx, pta_kernel_times *out);
 
 /* Batches: several contexts advanced by the same kernel launches (one set
  * of launches per fine step for all members, replayed from a CUDA graph).
- * Members must use the same stream and precision and belong to no other
+ * Members must use the same stream (precisions and sizes may differ) and belong to no other
  * batch; they stay usable on their own between batch calls. */
 int pta_batch_create(pta_ctx *const *members, int count, pta_batch **out);
 void pta_batch_destroy(pta_batch *batch);
@@ -336,6 +348,15 @@ int pta_batch_coarse_step(pta_batch *batch, pta_coarse_result *out);
 int pta_batch_tick(pta_batch *batch, pta_coarse_result *out);
 int pta_batch_set_timing(pta_batch *batch, int enable);
 int pta_batch_get_timing(pta_batch *batch, pta_kernel_times *out);
+
+/* Measurement helper (no counterpart in the paper): the fused multiply-add
+ * rate of the current GPU, the peak the pair kernels' roofline divides by.
+ * One launch fills every SM with threads that each run 16 independent FMA
+ * chains of `iters` steps; kind 0 = scalar FP32, 1 = packed FP32 (two
+ * lanes per instruction), 2 = FP64.  *flops gets the flop count (2 per FMA
+ * and lane), *ms the launch's CUDA-event time on `stream` (a cudaStream_t).
+ * Blocks until the launch is done. */
+int pta_measure_fma_rate(int kind, int64_t iters, void *stream, double *flops, double *ms);
 
 /* Neighbour lists without device allocation.
  *

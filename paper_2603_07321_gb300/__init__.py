@@ -25,7 +25,7 @@ __all__ = [
     "pta_apply_strain", "pta_fine_burst", "pta_coarse_step", "pta_get_state", "pta_set_state",
     "pta_forces", "pta_get_neighbours", "pta_get_series", "pta_save_state", "pta_load_state",
     "pta_batch_create", "pta_batch_destroy", "pta_batch_fine_burst", "pta_batch_apply_strain",
-    "pta_batch_coarse_step", "pta_batch_tick", "pta_footprint_bytes", "PREC_FP64",
+    "pta_batch_coarse_step", "pta_batch_tick", "pta_coarse_update", "pta_footprint_bytes", "PREC_FP64",
     "PREC_MIXED",
 ]
 
@@ -135,6 +135,7 @@ _SIGS = {
     "pta_get_series": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64,
                                       _P(ctypes.c_int64)]),
     "pta_coarse_step": (ctypes.c_int, [_VP, _P(CoarseResult)]),
+    "pta_coarse_update": (ctypes.c_int, [_VP, _P(ctypes.c_double), _P(CoarseResult)]),
     "pta_get_state": (ctypes.c_int, [_VP, _P(ctypes.c_double), _P(ctypes.c_double),
                                      ctypes.c_int64]),
     "pta_set_state": (ctypes.c_int, [_VP, _P(ctypes.c_double), _P(ctypes.c_double),
@@ -155,6 +156,8 @@ _SIGS = {
     "pta_get_timing": (ctypes.c_int, [_VP, _P(KernelTimes)]),
     "pta_batch_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pta_batch_get_timing": (ctypes.c_int, [_VP, _P(KernelTimes)]),
+    "pta_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _VP,
+                                            _P(ctypes.c_double), _P(ctypes.c_double)]),
     "pta_neighbours_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_double),
                                               _P(ctypes.c_double), ctypes.c_double,
                                               ctypes.c_int32, _VP, _VP, _P(ctypes.c_int32),
@@ -342,6 +345,14 @@ def pta_coarse_step(h) -> CoarseResult:
     return r
 
 
+def pta_coarse_update(h, means) -> CoarseResult:
+    """means: 3 x 3 (burst, variable) averages fed to the coarse-step update"""
+    m = np.ascontiguousarray(np.asarray(means, dtype=np.float64).reshape(9))
+    r = CoarseResult()
+    _check(load().pta_coarse_update(h, _dptr(m), ctypes.byref(r)), "pta_coarse_update")
+    return r
+
+
 def pta_get_state(h, n):
     pos = np.zeros((n, 3))
     vel = np.zeros((n, 3))
@@ -442,6 +453,19 @@ def pta_batch_get_timing(b) -> KernelTimes:
     return t
 
 
+def pta_measure_fma_rate(kind: int, iters: int, stream=None):
+    """(flops, ms) of one launch of FMA chains: kind 0 scalar FP32, 1 packed
+    FP32, 2 FP64."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    fl = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(load().pta_measure_fma_rate(int(kind), int(iters), _VP(stream), ctypes.byref(fl),
+                                       ctypes.byref(ms)), "pta_measure_fma_rate")
+    return fl.value, ms.value
+
+
 NOALLOC_MAX_ATOMS = 131072
 NOALLOC_MAX_CELLS = 65536
 
@@ -522,6 +546,9 @@ class Ctx:
 
     def coarse_step(self):
         return pta_coarse_step(self.h)
+
+    def coarse_update(self, means):
+        return pta_coarse_update(self.h, means)
 
     def get_state(self):
         return pta_get_state(self.h, self.n)

@@ -458,7 +458,9 @@ __global__ void k_pta_update(const SpecDev *__restrict__ specs, const int *__res
         for (int q = 0; q < 3; ++q) {
             const double Ra = P.R3[0][q], Rb = P.R3[1][q], Rc = P.R3[2][q];
             const double dvdt = (P.R_t[q] - P.R_tmD[q]) / D;  // Eq. (dvdt_algo)
-            const double vp = P.v[q] + h * dvdt;               // Eq. (pta_pred)
+            // Eq. (pta_pred), rounded as written (no fused multiply-add), so
+            // that the extrapolation is reproducible off the device
+            const double vp = __dadd_rn(P.v[q], __dmul_rn(h, dvdt));
             const double vd = (Ra + 4.0 * Rb + Rc) / 6.0;      // Eq. (simp)
             const double fl = S.floor_[q];
             const double ev = rel_err(vp, vd, fl);             // Eq. (rel_err)

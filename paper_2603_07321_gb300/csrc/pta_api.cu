@@ -37,7 +37,20 @@ double kb_ev() { return KB_SI / E_CHARGE; }
 double ev_a3_to_gpa() { return E_CHARGE / 1e-30 / 1e9; }
 
 constexpr int CHUNK = 64;
-constexpr int THREADS_TARGET = 152 * 2048;  // resident threads of a full GB300
+
+// resident threads of the whole current GPU (SM count x threads per SM, from
+// the device attributes); 0 when no device can be queried
+long long device_threads() {
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (long long)nsm * per_sm;
+}
 
 struct Allocator {
     pta_alloc_fn alloc = nullptr;
@@ -260,7 +273,11 @@ struct Sizes {
 // whole GPU; mixed-precision ones aim at ~64K threads and let batching fill
 // the device
 static int auto_lanes(long long n, int prec) {
-    const long long target = prec == PTA_PREC_FP64 ? THREADS_TARGET : 65536;
+    long long target = 65536;
+    if (prec == PTA_PREC_FP64) {
+        target = device_threads();
+        if (target <= 0) target = 1LL << 18;  // no device to ask: a full GPU of this class
+    }
     long long t = target / std::max<long long>(n, 1);
     int L = 1;
     while (L * 2 <= t && L < 16) L *= 2;
@@ -1334,6 +1351,37 @@ int pta_coarse_step(pta_ctx *c, pta_coarse_result *out) {
     rc = run_tick(r, out, 0);
     if (rc == PTA_ECUDA) c->broken = true;
     return rc;
+}
+
+int pta_coarse_update(pta_ctx *c, const double means[9], pta_coarse_result *out) {
+    if (!c || !means) return PTA_EINVAL;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(means[i])) return PTA_EINVAL;
+    Runner *r;
+    CKR(ctx_solo(c, &r));
+    // the three burst means go where the bursts' ends file them (slots 0..2
+    // of the slow-variable record), then the same update kernel runs
+    double *d_r3 = &c->hd.ctl->pta.R3[0][0];
+    CK(cudaMemcpyAsync(d_r3, means, 9 * sizeof(double), cudaMemcpyHostToDevice, r->stream));
+    const int op = c->pta_init ? 2 : 1;
+    r->h_ops[0] = op;
+    CK(cudaMemcpyAsync(r->d_ops, r->h_ops, sizeof(int), cudaMemcpyHostToDevice, r->stream));
+    launch_pta_update(r->tab, r->d_ops, r->d_cres, r->stream);
+    CKR(launch_check());
+    CK(cudaMemcpyAsync(r->h_cres, r->d_cres, sizeof(pta_coarse_result), cudaMemcpyDeviceToHost,
+                       r->stream));
+    CK(cudaStreamSynchronize(r->stream));
+    c->pta_init = true;
+    if (out) {
+        *out = r->h_cres[0];
+        out->strain = c->u / c->L_s;
+        for (int b = 0; b < 3; ++b) {
+            out->burst[b] = pta_averages{};
+            for (int q = 0; q < 3; ++q) out->burst[b].mean[q] = means[3 * b + q];
+        }
+        out->status = PTA_OK;
+    }
+    return PTA_OK;
 }
 
 int pta_get_state(pta_ctx *c, double *pos, double *vel, int64_t n) {

@@ -92,8 +92,8 @@ def test_observables_of_a_state(P, oracle):
     ctx.close()
 
 
-def _pair(P, oracle, shape, prec, seed, T0=300.0):
-    ctx = P.Ctx(shape, T0=T0, seed=seed, precision=prec)
+def _pair(P, oracle, shape, prec, seed, T0=300.0, **kw):
+    ctx = P.Ctx(shape, T0=T0, seed=seed, precision=prec, **kw)
     spec = oracle.Specimen(shape)
     spec.thermalise(T0, seed)
     if prec == P.PREC_MIXED:
@@ -106,7 +106,7 @@ def _pair(P, oracle, shape, prec, seed, T0=300.0):
 
 
 def test_trajectory_fp64_200_steps(P, oracle):
-    ctx, spec = _pair(P, oracle, (6, 6, 6), P.PREC_FP64, seed=11)
+    ctx, spec = _pair(P, oracle, (6, 6, 6), P.PREC_FP64, seed=11, block_steps=40)
     ctx.apply_strain(2e-3)
     spec.apply_strain(2e-3)
     a = ctx.fine_burst(200)
@@ -117,6 +117,16 @@ def test_trajectory_fp64_200_steps(P, oracle):
     assert np.max(np.abs(pos - spec.pos)) < 1e-8
     assert np.allclose(s_gpu, s_ref, rtol=1e-9, atol=1e-9)
     assert np.allclose(a.mean, s_ref.mean(axis=0), rtol=1e-12)
+    # block standard errors (5 blocks of 40 steps), element by element: against
+    # the oracle's estimator on the device's own samples (same numbers, so to
+    # rounding) and on the oracle's trajectory (which agrees to ~1e-9)
+    _, se_own = oracle.burst_averages(s_gpu, 40)
+    _, se_ref = oracle.burst_averages(s_ref, 40)
+    assert np.allclose(a.se, se_own, rtol=1e-10, atol=0)
+    # |SE(x) - SE(y)| <= max |x - y| over the samples (the sample standard
+    # deviation of block means is 1-Lipschitz in the largest sample difference)
+    dmax = np.max(np.abs(s_gpu - s_ref), axis=0)
+    assert np.all(np.abs(np.array(a.se) - se_ref) <= 1.01 * dmax + 1e-12)
     ctx.close()
 
 
@@ -313,3 +323,32 @@ def test_pruned_inner_list_changes_no_result(P, oracle):
     assert out[0][2] > 1 and out[1][2] == 0
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1][0], out[1][1][0])
+
+
+def test_batch_members_match_the_oracle(P, oracle):
+    # uneven sizes and both precisions in one batch; each member against its
+    # own oracle trajectory of 200 steps (not only against a solo GPU run)
+    cases = [((5, 5, 5), P.PREC_MIXED, 31), ((6, 4, 7), P.PREC_FP64, 32),
+             ((4, 6, 5), P.PREC_MIXED, 33), ((3, 3, 4), P.PREC_FP64, 34)]
+    pairs = [_pair(P, oracle, sh, pr, seed) for sh, pr, seed in cases]
+    members = [c for c, _ in pairs]
+    b = P.Batch(members)
+    d_eps = [1e-3, 2e-3, -1e-3, 3e-3]
+    b.apply_strain(d_eps)
+    res = b.fine_burst([200, 200, 200, 200])
+    for (ctx, spec), (sh, pr, _), de, r in zip(pairs, cases, d_eps, res):
+        spec.apply_strain(de)
+        s_ref = spec.burst(200)
+        s_gpu = ctx.series()
+        pos, _ = ctx.get_state()
+        assert r.nsteps == 200 and r.status == 0
+        if pr == P.PREC_FP64:
+            assert np.max(np.abs(pos - spec.pos)) < 1e-8
+            assert np.allclose(s_gpu, s_ref, rtol=1e-9, atol=1e-9)
+        else:
+            assert np.max(np.abs(pos - spec.pos)) < 1e-4 * 4.05 * sh[2]
+            assert np.allclose(s_gpu[:, :2], s_ref[:, :2], rtol=1e-5)
+            assert np.max(np.abs(s_gpu[:, 2] - s_ref[:, 2])) < 1e-3
+    b.close()
+    for m in members:
+        m.close()
