@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define PTA_ABI_VERSION 1
+#define PTA_ABI_VERSION 2
 
 typedef enum {
     PTA_OK = 0,
@@ -71,6 +71,22 @@ typedef enum {
 enum { PTA_POT_SUTTON_CHEN_SF = 1 };
 enum { PTA_PREC_FP64 = 0, PTA_PREC_MIXED = 1 };
 enum { PTA_SRC_PREDICTED = 0, PTA_SRC_MEASURE_JUMP = 1, PTA_SRC_MEASURE_MISMATCH = 2 };
+/* How the pair passes of Eqs. (pe) and (f_int) find each atom's neighbours.
+ *   PTA_PAIRS_LISTS: Verlet lists (cell binning by counting sort, a list of
+ *     every pair within rc + skin, rebuilt when an atom has moved skin / 2).
+ *   PTA_PAIRS_STENCIL (mixed precision): the lattice stencil.  The specimen
+ *     is a crystal built site by site, and while it keeps its lattice the
+ *     neighbour at lattice offset v of every atom is the atom at that
+ *     offset; atoms stay in lattice row order and the pair passes visit, for
+ *     every atom, the same set of offsets (every offset of a pair within
+ *     rc + stencil_skin at the last check; a check runs whenever an atom has
+ *     moved stencil_skin / 2, and at every burst start).  Pairs beyond rc
+ *     contribute nothing, so the sums are those of the equations, in another
+ *     order.  When a check finds offsets too wide or too many for the
+ *     stencil (the crystal has slipped), the specimen moves to Verlet lists
+ *     on the device before the next pair pass, and stays there.
+ *   PTA_PAIRS_AUTO: the stencil for mixed precision, lists for FP64. */
+enum { PTA_PAIRS_AUTO = 0, PTA_PAIRS_STENCIL = 1, PTA_PAIRS_LISTS = 2 };
 
 /* Specimen (problem-setup section; grips from the boundary-conditions
  * section).  n_cells >= 3 along the load axis and >= 1 along the others.
@@ -115,23 +131,17 @@ typedef struct {
     int neigh_cap;      /* neighbour-list capacity per atom, 0 = automatic     */
     int lanes;          /* threads per atom in the pair kernels: 0 = automatic,
                            else 1, 2, 4, 8 or 16                               */
-    int atoms_per_thread; /* atoms sharing one neighbour list and thread group in
-                           the mixed-precision kernels: 0 = automatic, 1 or 2
-                           (2 needs lanes 1 or 2; FP64 uses 1)                 */
+    int atoms_per_thread; /* atoms per thread group: 0 or 1 (2, two atoms sharing
+                           a union list, is no longer provided:
+                           PTA_EUNSUPPORTED)                                  */
     double prune_margin;  /* mixed precision: the pair passes read an inner list
                            of the pairs within rc + prune_margin, pruned from the
                            Verlet list whenever an atom has moved more than
                            prune_margin / 2 since the last pruning; it holds every
                            pair within rc in the same order, so results do not
                            change.  0 = default 0.3 A, < 0 = off               */
-    int cell_tiles;     /* mixed precision, one thread per atom: the pair passes
-                           take tiles of 2x2x2 cells per thread block and read
-                           the neighbours' records from a shared-memory copy of
-                           the 4x4x4 cells around the tile (per-atom results
-                           are unchanged).  1 = on (also makes the automatic
-                           lane count 1; PTA_EUNSUPPORTED for FP64,
-                           atoms_per_thread 2 or lanes > 1); 0 (default) and
-                           -1 = off                                          */
+    int cell_tiles;     /* 0 or -1; 1 (pair passes by shared-memory cell tiles) is
+                           no longer provided: PTA_EUNSUPPORTED              */
     int conv_lag;       /* adaptive burst length (appendix, Eq. (R_m_conv)):
                            every conv_lag steps from 2 conv_lag on, variable m
                            has converged once |R^(i) - R^(i-k)| /
@@ -142,6 +152,10 @@ typedef struct {
     int mean_positions; /* 1: also average every atom's position over the
                            states a burst samples (Eq. (mean_pos)), read with
                            pta_get_mean_positions; 0 (default) = off        */
+    int pair_scheme;    /* PTA_PAIRS_AUTO (default), _STENCIL (mixed precision
+                           only, else PTA_EUNSUPPORTED) or _LISTS            */
+    double stencil_skin;/* skin of the lattice stencil, A (0 = default 1 A;
+                           at most skin)                                     */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
@@ -224,13 +238,12 @@ int pta_natoms(const pta_ctx *ctx, int64_t *n);
  * (lanes), out[1] atoms per thread group, out[2] neighbour-list capacity per
  * atom, out[3] 1 when the pruned inner list is in use. */
 int pta_get_layout(const pta_ctx *ctx, int32_t out[4]);
-/* Cell tiles of this context (pta_params.cell_tiles): out[0] 1 when the pair
- * passes use them, out[1] thread blocks of a pair pass (each takes every
- * out[1]-th occupied tile), out[2] occupied tiles at the last list build,
- * out[3] of those, tiles whose surrounding cells hold at most 3328 atoms and
- * are read from the shared-memory copy (the others read global memory).
- * Zeros after out[0] when tiles are off. */
-int pta_get_tiling(pta_ctx *ctx, int32_t out[4]);
+/* The pair scheme of this context now: out[0] PTA_PAIRS_STENCIL or
+ * PTA_PAIRS_LISTS (a stencil context that has left the stencil reports
+ * lists), out[1] lattice offsets in the stencil (0 on lists), out[2] stencil
+ * checks since creation, out[3] threads per atom of the stencil kernels (0
+ * when the context cannot use the stencil). */
+int pta_get_scheme(pta_ctx *ctx, int32_t out[4]);
 /* 0 mobile, 1 left grip, 2 right grip; n must equal the atom count */
 int pta_get_flags(pta_ctx *ctx, uint8_t *flags, int64_t n);
 

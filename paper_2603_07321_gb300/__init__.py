@@ -34,6 +34,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpta.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+PAIRS_AUTO, PAIRS_STENCIL, PAIRS_LISTS = 0, 1, 2
 SRC_PREDICTED, SRC_MEASURE_JUMP, SRC_MEASURE_MISMATCH = 0, 1, 2
 
 _STATUS = {0: "PTA_OK", -1: "PTA_EINVAL", -2: "PTA_ENOMEM", -3: "PTA_ECUDA",
@@ -71,7 +72,8 @@ class Params(ctypes.Structure):
                 ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
                 ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int),
                 ("conv_lag", ctypes.c_int), ("conv_tol", ctypes.c_double * 3),
-                ("mean_positions", ctypes.c_int)]
+                ("mean_positions", ctypes.c_int), ("pair_scheme", ctypes.c_int),
+                ("stencil_skin", ctypes.c_double)]
 
 
 class Averages(ctypes.Structure):
@@ -124,7 +126,7 @@ _SIGS = {
     "pta_destroy": (None, [_VP]),
     "pta_natoms": (ctypes.c_int, [_VP, _P(ctypes.c_int64)]),
     "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
-    "pta_get_tiling": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
+    "pta_get_scheme": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_mean_positions": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64]),
     "pta_relax": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                  _P(Averages), _P(ctypes.c_int64)]),
@@ -290,10 +292,11 @@ def pta_get_layout(h) -> dict:
             "pruned_list": bool(out[3])}
 
 
-def pta_get_tiling(h) -> dict:
+def pta_get_scheme(h) -> dict:
     out = (ctypes.c_int32 * 4)()
-    _check(load().pta_get_tiling(h, out), "pta_get_tiling")
-    return {"tiled": bool(out[0]), "blocks": out[1], "tiles": out[2], "staged_tiles": out[3]}
+    _check(load().pta_get_scheme(h, out), "pta_get_scheme")
+    return {"scheme": {PAIRS_STENCIL: "stencil", PAIRS_LISTS: "lists"}.get(out[0], "?"),
+            "keys": out[1], "checks": out[2], "stencil_lanes": out[3]}
 
 
 def pta_relax(h, window: int, max_steps: int, tol_gpa: float):
@@ -522,8 +525,8 @@ class Ctx:
     def layout(self):
         return pta_get_layout(self.h)
 
-    def tiling(self):
-        return pta_get_tiling(self.h)
+    def scheme(self):
+        return pta_get_scheme(self.h)
 
     def mean_positions(self):
         return pta_get_mean_positions(self.h, self.n)

@@ -21,6 +21,7 @@ namespace pta {
 
 __device__ __forceinline__ bool build_active(const SpecDev &S, int force) {
     const SpecCtl *c = S.ctl;
+    if (c->scheme != SCHEME_LIST) return false;
     if (force) return true;
     if (c->phase == PH_IDLE) return false;
     return c->rebuild != 0 || c->list_L != S.L;
@@ -56,7 +57,7 @@ __global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__
     int ci[3];
     for (int d = 0; d < 3; ++d)
         ci[d] = clampi((int)floor((x[d] - S.org[d]) * S.inv_h), 0, S.nc[d] - 1);
-    const int c = cell_rank(S.tiled, S.nc, ci[0], ci[1], ci[2]);
+    const int c = cell_rank(S.nc, ci[0], ci[1], ci[2]);
     S.atom_cell[a] = c;
     atomicAdd(&S.cell_cnt[c], 1);
 }
@@ -66,171 +67,7 @@ __global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__
 __global__ void k_scan(const SpecDev *__restrict__ specs, int force) {
     const SpecDev &S = specs[blockIdx.x];
     if (!build_active(S, force)) return;
-    __shared__ int wsum[SCAN_THREADS / 32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    if (S.G == 2) {
-        // units per cell, (count + 1) / 2, scanned into unit_cell
-        __shared__ int ucarry;
-        if (threadIdx.x == 0) ucarry = 0;
-        __syncthreads();
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
-            const int c = base + threadIdx.x;
-            const int v = (c < S.ncell) ? (S.cell_cnt[c] + 1) / 2 : 0;
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) wsum[w] = x;
-            __syncthreads();
-            if (w == 0) {
-                int t = wsum[lane];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o) t += y;
-                }
-                wsum[lane] = t;
-            }
-            __syncthreads();
-            const int excl = ucarry + (w ? wsum[w - 1] : 0) + x - v;
-            if (c < S.ncell) S.unit_cell[c] = excl;
-            __syncthreads();
-            if (threadIdx.x == SCAN_THREADS - 1) ucarry = excl + v;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            S.unit_cell[S.ncell] = ucarry;
-            S.ctl->nunits = ucarry;
-        }
-        __syncthreads();
-    } else if (threadIdx.x == 0) {
-        S.ctl->nunits = S.n;
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
-        const int c = base + threadIdx.x;
-        const int v = (c < S.ncell) ? S.cell_cnt[c] : 0;
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            int s = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            wsum[lane] = s;  // inclusive over warps
-        }
-        __syncthreads();
-        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
-        if (c < S.ncell) {
-            S.cell_start[c] = excl;
-            S.cell_cnt[c] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        S.cell_start[S.ncell] = carry;
-        S.ctl->rebuilds += 1;
-    }
-    if (!S.tiled) return;
-    // occupied tiles, in rank order (the cell starts above are visible to
-    // the whole block after the barrier)
-    __syncthreads();
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < S.ntile_grid; base += SCAN_THREADS) {
-        const int b = base + threadIdx.x;
-        const int v = (b < S.ntile_grid && S.cell_start[8 * b + 8] > S.cell_start[8 * b]) ? 1 : 0;
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            int t = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            wsum[lane] = t;
-        }
-        __syncthreads();
-        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
-        if (v) S.tile_list[excl] = b;
-        __syncthreads();
-        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) S.ctl->ntiles = carry;
-}
-
-// one warp per occupied tile: its atom range and the halo table (stage
-// offset and first slot of each of the 4x4x4 cells around it, cells outside
-// the grid empty); the halo is staged when it holds at most TILE_SC atoms
-__global__ void k_tile_table(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
-                             int force) {
-    const SpecDev &S = specs[b2s[blockIdx.x]];
-    if (!S.tiled || !build_active(S, force)) return;
-    const int lane = threadIdx.x & 31;
-    const int nwarp = S.nblk_atom * (TPB / 32);
-    const int nt = S.ctl->ntiles;
-    for (int k = (blockIdx.x - S.blk_atom0) * (TPB / 32) + (threadIdx.x >> 5); k < nt; k += nwarp) {
-        const int b = S.tile_list[k];
-        int bx, by, bz;
-        tile_coords(S.nc, b, bx, by, bz);
-        int cnt[2], st[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int hc = 2 * lane + i;
-            const int x = 2 * bx - 1 + (hc & 3), y = 2 * by - 1 + ((hc >> 2) & 3),
-                      z = 2 * bz - 1 + (hc >> 4);
-            cnt[i] = 0;
-            st[i] = 0;
-            if (x >= 0 && y >= 0 && z >= 0 && x < S.nc[0] && y < S.nc[1] && z < S.nc[2]) {
-                const int c = cell_rank(S.tiled, S.nc, x, y, z);
-                st[i] = S.cell_start[c];
-                cnt[i] = S.cell_start[c + 1] - st[i];
-            }
-        }
-        const int v = cnt[0] + cnt[1];
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        const int excl = x - v;
-        const int total = __shfl_sync(0xffffffffu, x, 31);
-        int *T = S.tile_tab + (long long)b * TT_STRIDE;
-        T[TT_OFF + 2 * lane] = excl;
-        T[TT_OFF + 2 * lane + 1] = excl + cnt[0];
-        T[TT_START + 2 * lane] = st[0];
-        T[TT_START + 2 * lane + 1] = st[1];
-        if (lane == 0) {
-            T[TT_OFF + TILE_HALO] = total;
-            T[TT_A0] = S.cell_start[8 * b];
-            T[TT_A1] = S.cell_start[8 * b + 8];
-            T[TT_STAGED] = total <= TILE_SC ? 1 : 0;
-        }
-    }
+    scan_cells(S);
 }
 
 __global__ void k_scatter(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
@@ -281,13 +118,13 @@ __global__ void k_permute_gather(const SpecDev *__restrict__ specs, const int *_
     const int par = S.ctl->parity;
     const PermLayout Lo = perm_layout(S.n, S.prec);
     char *t = (char *)S.perm_tmp;
+    // velocities: 32-byte records in both precisions (double4 or VelHL)
+    ((double4_32a *)(t + Lo.vel))[p] = ((const double4_32a *)S.vel)[src];
     if (S.prec == PTA_PREC_FP64) {
         ((double4_32a *)(t + Lo.pos))[p] = ((const double4_32a *)S.pos[par])[src];
-        ((double4_32a *)(t + Lo.vel))[p] = ((const double4_32a *)S.vel)[src];
     } else {
         ((float4 *)(t + Lo.pos))[p] = ((const float4 *)S.pos[par])[src];
         ((float4 *)(t + Lo.lo))[p] = S.lo[par][src];
-        ((float4 *)(t + Lo.vel))[p] = ((const float4 *)S.vel)[src];
     }
     ((uint8_t *)(t + Lo.flags))[p] = S.flags[src];
     ((int *)(t + Lo.orig))[p] = S.orig[src];
@@ -303,32 +140,16 @@ __global__ void k_permute_scatter(const SpecDev *__restrict__ specs, const int *
     const int par = S.ctl->parity;
     const PermLayout Lo = perm_layout(S.n, S.prec);
     const char *t = (const char *)S.perm_tmp;
+    ((double4_32a *)S.vel)[p] = ((const double4_32a *)(t + Lo.vel))[p];
     if (S.prec == PTA_PREC_FP64) {
         ((double4_32a *)S.pos[par])[p] = ((const double4_32a *)(t + Lo.pos))[p];
-        ((double4_32a *)S.vel)[p] = ((const double4_32a *)(t + Lo.vel))[p];
     } else {
         ((float4 *)S.pos[par])[p] = ((const float4 *)(t + Lo.pos))[p];
         S.lo[par][p] = ((const float4 *)(t + Lo.lo))[p];
-        ((float4 *)S.vel)[p] = ((const float4 *)(t + Lo.vel))[p];
     }
     S.flags[p] = ((const uint8_t *)(t + Lo.flags))[p];
     S.orig[p] = ((const int *)(t + Lo.orig))[p];
     S.atom_cell[p] = ((const int *)(t + Lo.cell))[p];
-}
-
-// G = 2: pair up the atoms of every cell (slots 2k, 2k+1 of the cell form a
-// unit; an odd cell ends with a one-atom unit), so a unit never spans cells
-__global__ void k_unit_table(const SpecDev *__restrict__ specs, const int *__restrict__ b2s,
-                             int force) {
-    const SpecDev &S = specs[b2s[blockIdx.x]];
-    if (S.G != 2 || !build_active(S, force)) return;
-    const int p = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
-    if (p >= S.n) return;
-    const int c = S.atom_cell[p];
-    const int r = p - S.cell_start[c];
-    if (r & 1) return;
-    const int cnt = S.cell_start[c + 1] - S.cell_start[c];
-    S.unit_first[S.unit_cell[c] + r / 2] = p | ((r + 1 < cnt) ? UNIT_SECOND : 0);
 }
 
 // mixed precision: every atom's half-cell in its new cell, its neighbour
@@ -384,10 +205,9 @@ __device__ __forceinline__ bool in_list(const SpecDev &S, int par, bool mixed, i
     return r2 < S.rl2;
 }
 
-// one thread per unit of G consecutive atoms: the unit's list is the union of
-// its atoms' lists (every j within the list radius of at least one atom of
-// the unit other than j itself), gathered from the box of cells around the
-// unit's cells in (z, y, x) order, each cell's atoms in slot order
+// one thread per atom (per lane group): every j != i within the list radius,
+// gathered from the 27 cells around the atom's cell in (z, y, x) order, each
+// cell's atoms in slot order
 __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs,
                                                const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -395,15 +215,14 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
     const int u = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
     const int par = S.ctl->parity;
     int cnt = 0;
-    if (S.G == 1 && S.L == 1 && S.prec != PTA_PREC_FP64) {
+    if (S.L == 1 && S.prec != PTA_PREC_FP64) {
         // warp-uniform loop over the 27 cells around each atom's cell; the
         // FP32 candidate test uses the cell-relative records, the FP64 test
         // decides the thin band around the list radius; list rows are staged
         // in shared memory and written whole
         __shared__ int rowbuf[TPB / 32][RW_ROWS * 32];
         const int lane = threadIdx.x & 31;
-        const int nu = S.ctl->nunits;
-        const bool valid = u < nu;
+        const bool valid = u < S.n;
         const int a = valid ? u : 0;
         RowWriter<RW_ROWS> wr;
         wr.buf = rowbuf[threadIdx.x >> 5];
@@ -425,12 +244,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                      za = (double)ha.z + (double)la.z;
         const int ca = S.atom_cell[a];
         int cx, cy, cz;
-        cell_coords(S.tiled, S.nc, ca, cx, cy, cz);
-        // tiled: entries of a staged tile index its halo copy; halo cell of
-        // the neighbour cell at offset d is (own cell in the tile + 1 + d)
-        const int *__restrict__ Tt = S.tiled ? S.tile_tab + (long long)(ca >> 3) * TT_STRIDE : nullptr;
-        const bool staged = Tt != nullptr && Tt[TT_STAGED] != 0;
-        const int hown = (1 + (ca & 1)) + 4 * (1 + ((ca >> 1) & 1)) + 16 * (1 + ((ca >> 2) & 1));
+        cell_coords(S.nc, ca, cx, cy, cz);
         const float h = S.f_h;
         // a warp past the last atom writes nothing: its tile lies beyond the
         // list (and the rows every lane has passed are unbounded)
@@ -442,11 +256,10 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                     const bool inside = valid && xx >= 0 && yy >= 0 && zz >= 0 && xx < S.nc[0] &&
                                         yy < S.nc[1] && zz < S.nc[2];
                     if (inside) {
-                        const int cc = cell_rank(S.tiled, S.nc, xx, yy, zz);
+                        const int cc = cell_rank(S.nc, xx, yy, zz);
                         const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
                         // half-cell offset 2d + sub_j - sub_a: add the spread bits of j
                         const unsigned code = nl_entry(0, 2 * dx, 2 * dy, 2 * dz) - (unsigned)own_sub;
-                        const int shift = staged ? Tt[TT_OFF + hown + dx + 4 * dy + 16 * dz] - s : 0;
                         // position of atom a relative to the centre of cell cc
                         const float ox = ra.x - (float)dx * h, oy = ra.y - (float)dy * h,
                                     oz = ra.z - (float)dz * h;
@@ -463,7 +276,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                                 in = in_list(S, par, true, a, xa, ya, za, ha, la, j);
                             if (in && j != a) {
                                 if (cnt < S.cap_use)
-                                    wr.put(cnt, (int)(((unsigned)(j + shift) << NL_CODE_BITS) +
+                                    wr.put(cnt, (int)(((unsigned)j << NL_CODE_BITS) +
                                                       code + (unsigned)__float_as_int(rj.w)));
                                 ++cnt;
                             }
@@ -481,53 +294,40 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
             S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
             S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
         }
-    } else if (u < S.ctl->nunits) {
+    } else if (u < S.n) {
         const bool mixed = S.prec != PTA_PREC_FP64;
-        int a0, ga;
-        unit_atoms(S, u, a0, ga);
-        double x[2], y[2], z[2];
-        float4 ha[2], la[2];
-        int cx[2], cy[2], cz[2];
-        for (int g = 0; g < ga; ++g) {
-            load_pos64(S, par, a0 + g, x[g], y[g], z[g]);
-            ha[g] = la[g] = make_float4(0, 0, 0, 0);
-            if (mixed) {
-                ha[g] = ((const float4 *)S.pos[par])[a0 + g];
-                la[g] = S.lo[par][a0 + g];
-            }
-            cell_coords(S.tiled, S.nc, S.atom_cell[a0 + g], cx[g], cy[g], cz[g]);
+        const int a = u;
+        double x, y, z;
+        load_pos64(S, par, a, x, y, z);
+        float4 ha = make_float4(0, 0, 0, 0), la = make_float4(0, 0, 0, 0);
+        if (mixed) {
+            ha = ((const float4 *)S.pos[par])[a];
+            la = S.lo[par][a];
         }
-        int lo[3] = {cx[0], cy[0], cz[0]}, hi[3] = {cx[0], cy[0], cz[0]};
-        for (int g = 1; g < ga; ++g) {
-            lo[0] = min(lo[0], cx[g]);
-            hi[0] = max(hi[0], cx[g]);
-            lo[1] = min(lo[1], cy[g]);
-            hi[1] = max(hi[1], cy[g]);
-            lo[2] = min(lo[2], cz[g]);
-            hi[2] = max(hi[2], cz[g]);
-        }
+        int cx, cy, cz;
+        cell_coords(S.nc, S.atom_cell[a], cx, cy, cz);
         const long long base = nl_base(u, S.L, S.cap);
         const int L = S.L;
-        // mixed: half-cell offsets from the unit's first atom (its atoms share a cell)
-        const int sub0 = mixed ? sub_spread(S.hsub[a0]) : 0;
-        for (int zz = max(lo[2] - 1, 0); zz <= min(hi[2] + 1, S.nc[2] - 1); ++zz)
-            for (int yy = max(lo[1] - 1, 0); yy <= min(hi[1] + 1, S.nc[1] - 1); ++yy)
-                for (int xx = max(lo[0] - 1, 0); xx <= min(hi[0] + 1, S.nc[0] - 1); ++xx) {
-                    const int cc = cell_rank(S.tiled, S.nc, xx, yy, zz);
+        // mixed: half-cell offsets from the atom's half-cell
+        const int sub0 = mixed ? sub_spread(S.hsub[a]) : 0;
+        for (int zz = max(cz - 1, 0); zz <= min(cz + 1, S.nc[2] - 1); ++zz)
+            for (int yy = max(cy - 1, 0); yy <= min(cy + 1, S.nc[1] - 1); ++yy)
+                for (int xx = max(cx - 1, 0); xx <= min(cx + 1, S.nc[0] - 1); ++xx) {
+                    const int cc = cell_rank(S.nc, xx, yy, zz);
                     const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
                     const unsigned code =
-                        mixed ? nl_entry(0, 2 * (xx - cx[0]), 2 * (yy - cy[0]), 2 * (zz - cz[0])) -
+                        mixed ? nl_entry(0, 2 * (xx - cx), 2 * (yy - cy), 2 * (zz - cz)) -
                                     (unsigned)sub0
-                              : nl_entry(0, xx - cx[0], yy - cy[0], zz - cz[0]);
-                    if (mixed && S.G == 1) {
-                        // one atom: the candidate test on the cell-relative records
-                        // (as in the one-lane path), the FP64 test for the thin band
+                              : nl_entry(0, xx - cx, yy - cy, zz - cz);
+                    if (mixed) {
+                        // the candidate test on the cell-relative records (as in
+                        // the one-lane path), the FP64 test for the thin band
                         const float4 *__restrict__ crec = (const float4 *)S.posfp;
-                        const float4 ra = crec[a0];
+                        const float4 ra = crec[a];
                         const float h = S.f_h;
-                        const float ox = ra.x - (float)(xx - cx[0]) * h,
-                                    oy = ra.y - (float)(yy - cy[0]) * h,
-                                    oz = ra.z - (float)(zz - cz[0]) * h;
+                        const float ox = ra.x - (float)(xx - cx) * h,
+                                    oy = ra.y - (float)(yy - cy) * h,
+                                    oz = ra.z - (float)(zz - cz) * h;
                         for (int j = s; j < e; ++j) {
                             const float4 rj = crec[j];
                             const float fx = rj.x - ox, fy = rj.y - oy, fz = rj.z - oz;
@@ -538,8 +338,8 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                             else if (r2f >= S.f_rl2_hi)
                                 in = false;
                             else
-                                in = in_list(S, par, true, a0, x[0], y[0], z[0], ha[0], la[0], j);
-                            if (in && j != a0) {
+                                in = in_list(S, par, true, a, x, y, z, ha, la, j);
+                            if (in && j != a) {
                                 if (cnt < S.cap_use)
                                     S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
                                         (int)(((unsigned)j << NL_CODE_BITS) + code +
@@ -550,22 +350,16 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                         continue;
                     }
                     for (int j = s; j < e; ++j) {
-                        bool in = false;
-                        for (int g = 0; g < ga && !in; ++g)
-                            in = (j != a0 + g) && in_list(S, par, mixed, a0 + g, x[g], y[g], z[g],
-                                                          ha[g], la[g], j);
-                        if (in) {
-                            const unsigned cj = mixed ? code + (unsigned)sub_spread(S.hsub[j]) : code;
+                        if (j != a && in_list(S, par, false, a, x, y, z, ha, la, j)) {
                             if (cnt < S.cap_use)
                                 S.nlist[base + (long long)(cnt / L) * 32 + (cnt % L)] =
-                                    (int)(((unsigned)j << NL_CODE_BITS) + cj);
+                                    (int)(((unsigned)j << NL_CODE_BITS) + code);
                             ++cnt;
                         }
                     }
                 }
         S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
-        for (int g = 0; g < ga; ++g)
-            S.ref[a0 + g] = make_float4((float)x[g], (float)y[g], (float)z[g], 0.f);
+        S.ref[a] = make_float4((float)x, (float)y, (float)z, 0.f);
     }
     // block maximum of the counts, one atomic per block
     __shared__ int smax[TPB / 32];
@@ -599,15 +393,18 @@ __global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
     if (threadIdx.x == 0) S.ctl->max_nn = 0;
 }
 
-// one block: does any specimen of the table need a list build, or only a
-// pruning of its inner list, before its next pair pass?  Sets the condition
-// of the graph node that holds that work (LIST_BUILD, LIST_PRUNE, LIST_NONE).
+// one block: does any specimen of the table need a list build or a stencil
+// check, or only a pruning of its inner list, before its next pair pass?
+// Sets the condition of the graph node that holds that work (LIST_BUILD,
+// LIST_PRUNE, LIST_NONE).
 __global__ void k_decide_rebuild(const SpecDev *__restrict__ specs, int nspec,
                                  cudaGraphConditionalHandle handle) {
     int build = 0, prune = 0;
     for (int s = threadIdx.x; s < nspec; s += blockDim.x) {
-        build |= build_active(specs[s], 0);
-        prune |= prune_active(specs[s], 0);
+        const SpecCtl *c = specs[s].ctl;
+        build |= build_active(specs[s], 0) ||
+                 (c->scheme == SCHEME_STENCIL && c->phase != PH_IDLE && c->rebuild != 0);
+        prune |= c->scheme == SCHEME_LIST && prune_active(specs[s], 0);
     }
     build = __syncthreads_or(build);
     prune = __syncthreads_or(prune);
@@ -627,8 +424,6 @@ void launch_rebuild(const Tab &t, int force, cudaStream_t st) {
     k_cell_sort<<<t.nblk_cell, CELL_WARPS * 32, 0, st>>>(t.specs, t.b2s_cell, force);
     k_permute_gather<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_permute_scatter<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
-    k_unit_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
-    k_tile_table<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_rel_all<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build<<<t.nblk_atom, TPB, 0, st>>>(t.specs, t.b2s_atom, force);
     k_build_done<<<t.nspec, 32, 0, st>>>(t.specs, force);

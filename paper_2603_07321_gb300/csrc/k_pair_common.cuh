@@ -29,8 +29,9 @@ __device__ __forceinline__ T lane_sum(T v) {
 }
 
 // Called by every thread of a pair block of NT threads after the warp
-// reductions (values valid in lane 0 of each warp).  Block partials go to
-// S.part (8 doubles per block); the last block of the specimen to finish
+// reductions (values valid in lane 0 of each warp); nblk is the number of
+// the specimen's blocks in this launch.  Block partials go to S.part (8
+// doubles per block); the last block of the specimen to finish
 // sums all partials in a fixed order (each thread a strided share, then
 // warp shuffles, then the warps in order) and advances the specimen's
 // control block:
@@ -41,9 +42,9 @@ __device__ __forceinline__ T lane_sum(T v) {
 // and in MODE_STEP the position buffers swap, the skin test sets the
 // rebuild flag and the pruning margin test the prune flag.
 template <int NT>
-__device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double pe_w, double rr_w,
-                                 double d2_w, double dp2_w, int mode, int phase, long long done,
-                                 long long nsteps) {
+__device__ inline void step_tail(const SpecDev &S, int lb, int nblk, double ke_w, double pe_w,
+                                 double rr_w, double d2_w, double dp2_w, int mode, int phase,
+                                 long long done, long long nsteps) {
     constexpr int NV = 5;  // K, U, R, max displacement^2 since the build and since the pruning
     constexpr int NW = NT / 32;
     __shared__ double shw[NV][NW];
@@ -74,13 +75,13 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
         P[4] = e;
         __threadfence();
         const unsigned prev = atomicAdd(&S.ctl->blocks_done, 1u);
-        is_last = (prev == (unsigned)(S.nblk_pair - 1));
+        is_last = (prev == (unsigned)(nblk - 1));
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     double v[NV] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < S.nblk_pair; b += NT) {
+    for (int b = threadIdx.x; b < nblk; b += NT) {
         const double *P = S.part + 8LL * b;
         v[0] = v[0] + __ldcg(P);
         v[1] = v[1] + __ldcg(P + 1);
@@ -156,7 +157,10 @@ __device__ inline void step_tail(const SpecDev &S, int lb, double ke_w, double p
         } else if (phase == PH_REFRESH) {
             c->phase = PH_RUN;
         }
-        c->rebuild = (md2 > (double)S.half_skin2) ? 1 : 0;
+        // the skin test: the list skin, or the stencil's own skin
+        const double hs2 = c->scheme == SCHEME_STENCIL ? (double)S.st_half_skin2
+                                                       : (double)S.half_skin2;
+        c->rebuild = (md2 > hs2) ? 1 : 0;
         if (S.prune_on && mp2 > (double)S.half_prune2) c->prune = 1;
         c->parity ^= 1;
     }

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
     pe = warp_sum(pe);
     rr = warp_sum(rr);
     d2 = (double)warp_max((float)d2);
-    step_tail<TPB>(S, lb, ke, pe, rr, d2, 0.0, mode, phase, done, nsteps);
+    step_tail<TPB>(S, lb, S.nblk_pair, ke, pe, rr, d2, 0.0, mode, phase, done, nsteps);
 }
 
 void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st) {

@@ -219,7 +219,12 @@ __global__ void k_import(const SpecDev *__restrict__ sp) {
         if (!ok) atomicOr(&S.ctl->err, ERR_RANGE);
         ((float4 *)S.pos[par])[a] = make_float4(h[0], h[1], h[2], 0.f);
         S.lo[par][a] = make_float4(l[0], l[1], l[2], 0.f);
-        ((float4 *)S.vel)[a] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        // v = vh + vl: the FP32 rounding and its remainder (exact to ~2^-48 v)
+        VelHL w;
+        w.h = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        w.l = make_float4((float)(v[0] - (double)w.h.x), (float)(v[1] - (double)w.h.y),
+                          (float)(v[2] - (double)w.h.z), 0.f);
+        ((VelHL *)S.vel)[a] = w;
     }
     if (a == 0) S.ctl->rebuild = 1;
 }
@@ -244,14 +249,58 @@ __global__ void k_export(const SpecDev *__restrict__ sp) {
     } else {
         const float4 h = ((const float4 *)S.pos[par])[a];
         const float4 l = S.lo[par][a];
-        const float4 w = ((const float4 *)S.vel)[a];
+        const VelHL w = ((const VelHL *)S.vel)[a];
         p[0] = (double)h.x + (double)l.x;
         p[1] = (double)h.y + (double)l.y;
         p[2] = (double)h.z + (double)l.z;
-        v[0] = w.x;
-        v[1] = w.y;
-        v[2] = w.z;
+        v[0] = (double)w.h.x + (double)w.l.x;
+        v[1] = (double)w.h.y + (double)w.l.y;
+        v[2] = (double)w.h.z + (double)w.l.z;
     }
+}
+
+// checkpoints: the raw working state (current position buffer, velocities,
+// grip flags) gathered into creation order through the permutation scratch,
+// or scattered back to the context's current slot order, so that a
+// checkpoint does not depend on how atoms are ordered in memory (by cell
+// for the lists, by lattice row for the stencil)
+__global__ void k_ckpt_move(const SpecDev *__restrict__ sp, int gather) {
+    const SpecDev &S = *sp;
+    const int a = blockIdx.x * TPB + threadIdx.x;
+    if (a >= S.n) return;
+    const int par = S.ctl->parity;
+    const int o = S.orig[a];
+    const PermLayout Lo = perm_layout(S.n, S.prec);
+    char *t = (char *)S.perm_tmp;
+    double4_32a *tv = (double4_32a *)(t + Lo.vel);
+    uint8_t *tf = (uint8_t *)(t + Lo.flags);
+    if (S.prec == PTA_PREC_FP64) {
+        double4_32a *tp = (double4_32a *)(t + Lo.pos);
+        double4_32a *wp = (double4_32a *)S.pos[par];
+        if (gather) tp[o] = wp[a]; else wp[a] = tp[o];
+    } else {
+        float4 *tp = (float4 *)(t + Lo.pos), *tl = (float4 *)(t + Lo.lo);
+        float4 *wp = (float4 *)S.pos[par];
+        if (gather) {
+            tp[o] = wp[a];
+            tl[o] = S.lo[par][a];
+        } else {
+            wp[a] = tp[o];
+            S.lo[par][a] = tl[o];
+        }
+    }
+    double4_32a *wv = (double4_32a *)S.vel;
+    if (gather) {
+        tv[o] = wv[a];
+        tf[o] = S.flags[a];
+    } else {
+        wv[a] = tv[o];
+        S.flags[a] = tf[o];
+    }
+}
+
+void launch_ckpt_move(const SpecDev &h, const SpecDev *d, int gather, cudaStream_t st) {
+    k_ckpt_move<<<(h.n + TPB - 1) / TPB, TPB, 0, st>>>(d, gather);
 }
 
 // end of thermal relaxation: the right grip is fixed where it is, v = 0
@@ -259,10 +308,8 @@ __global__ void k_fix_right_grip(const SpecDev *__restrict__ sp) {
     const SpecDev &S = *sp;
     const int a = blockIdx.x * TPB + threadIdx.x;
     if (a >= S.n || S.flags[a] != FLAG_RIGHT) return;
-    if (S.prec == PTA_PREC_FP64)
-        ((double4_32a *)S.vel)[a] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    else
-        ((float4 *)S.vel)[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // both precisions keep 32-byte velocity records (double4 or VelHL)
+    ((double4_32a *)S.vel)[a] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
 }
 
 void launch_fix_right_grip(const SpecDev &h, const SpecDev *d, cudaStream_t st) {

@@ -259,13 +259,17 @@ static PotDev make_pot(const pta_potential &p) {
 // sizes
 // ---------------------------------------------------------------------------
 struct Sizes {
-    long long n, nunits;
-    int L, G, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
-    int prune_on, tiled, ntile_grid, mean_pos;
+    long long n;
+    int L, cap, cap_use, nblk_pair, nblk_atom, nblk_cell, ncell, nc[3];
+    int prune_on, mean_pos;
     double prune_margin;
     double h, org[3];
     size_t list_words;
     long long series_cap;
+    // lattice stencil
+    int stencil, Lst, nblk_st, NKp, NYp, NZp;
+    long long nslot;
+    double st_skin;
 };
 
 // threads per atom chosen from the specimen alone (so that a specimen runs
@@ -289,20 +293,7 @@ static int valid_lanes(int L) { return L == 1 || L == 2 || L == 4 || L == 8 || L
 static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pta_params &par,
                          Sizes *z) {
     z->n = 4LL * s.n_cells[0] * s.n_cells[1] * s.n_cells[2];
-    z->L = par.lanes ? par.lanes
-                     : (par.cell_tiles == 1 ? 1 : auto_lanes(z->n, par.precision));
-    // atoms per thread group: 1 unless asked for 2 (two atoms of one cell
-    // sharing a union list read each neighbour record once for both, but the
-    // two per-atom branches per entry cost more issue slots than the saved
-    // reads on GB300, measured on the 470,596-atom cube)
-    z->G = par.atoms_per_thread ? par.atoms_per_thread : 1;
-    z->nunits = z->n;  // capacity; G = 2 sets the exact count at every build (below)
-    // cell tiles only on request: on GB300 their shared-memory gathers take
-    // as many L1 wavefronts as the global gathers they replace (8-9 per warp
-    // request from bank conflicts), and the 384-thread tile blocks run at
-    // lower occupancy, so they measured slower on the 470,596-atom cube
-    z->tiled = (par.precision == PTA_PREC_MIXED && z->G == 1 && z->L == 1 && par.cell_tiles == 1)
-                   ? 1 : 0;
+    z->L = par.lanes ? par.lanes : auto_lanes(z->n, par.precision);
     z->mean_pos = par.mean_positions ? 1 : 0;
     const double rl = p.rc + par.skin;
     z->prune_margin = par.prune_margin == 0.0 ? 0.3 : par.prune_margin;
@@ -311,18 +302,15 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     if (par.neigh_cap > 0) {
         z->cap_use = (int)round_up((size_t)par.neigh_cap, 32);
     } else {
-        // atoms of one unit lie within ~3 A of each other: the union list
-        // covers a sphere about 1.6 A wider
         const double dens = 4.0 / (s.a0 * s.a0 * s.a0);
-        const double rr = rl + (z->G > 1 ? 1.6 : 0.0);
-        const double nb = 4.0 / 3.0 * 3.141592653589793 * rr * rr * rr * dens;
+        const double nb = 4.0 / 3.0 * 3.141592653589793 * rl * rl * rl * dens;
         z->cap_use = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
     }
-    // eight spare iterations per unit: the pair loops read up to four
+    // eight spare iterations per atom: the pair loops read up to four
     // entries ahead without bounds tests (spare entries hold earlier, valid
     // indices or 0)
     z->cap = z->cap_use + 8 * z->L;
-    z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
+    z->nblk_pair = (int)((z->n * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
     // cell edge a multiple of 2^-11 A and grid origin on the 2^-12 A grid, so
     // that cell centres and centre differences are exact in FP32
@@ -338,37 +326,36 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     for (int d = 0; d < 3; ++d) {
         z->org[d] = std::floor(-margin * 4096.0) / 4096.0;
         z->nc[d] = (int)std::floor((span[d] + 2.0 * margin) / z->h) + 1;
-        z->nc[d] += z->nc[d] & 1;  // whole tiles of 2x2x2 cells
+        z->nc[d] += z->nc[d] & 1;
         ncell *= z->nc[d];
     }
     if (ncell > (1LL << 30)) return PTA_EINVAL;
     z->ncell = (int)ncell;
-    z->ntile_grid = (int)(ncell / 8);
     z->nblk_cell = (z->ncell + CELL_WARPS * CELLS_PER_WARP - 1) / (CELL_WARPS * CELLS_PER_WARP);
-    // G = 2: at most one one-atom unit per cell besides the pairs
-    if (z->G == 2) z->nunits = std::min<long long>(z->n, (z->n + 1) / 2 + z->ncell);
-    z->nblk_pair = (int)((z->nunits * z->L + TPB - 1) / TPB);
-    if (z->tiled) {
-        // one block per tile the specimen can occupy: an extent E meets at
-        // most floor(E / 2h) + 2 tiles per axis (10% more extent along the
-        // load axis for the strain); blocks loop when more tiles are occupied
-        long long nb = 1;
-        for (int d = 0; d < 3; ++d) {
-            const double ext = span[d] * (d == s.load_axis ? 1.1 : 1.0);
-            long long k = (long long)std::floor(ext / (2.0 * z->h)) + 2;
-            nb *= std::min<long long>(k, z->nc[d] / 2);
-        }
-        z->nblk_pair = (int)nb;
-    }
+    // words of the list: the layout of L lanes, or of one lane (the stencil's
+    // lists for pta_get_neighbours), whichever is larger
     const long long W = 32 / z->L;
-    z->list_words = (size_t)((z->nunits + W - 1) / W) * W * z->cap;
+    z->list_words = std::max<size_t>((size_t)((z->n + W - 1) / W) * W * z->cap,
+                             (size_t)((z->n + 31) / 32) * 32 * z->cap);
     z->series_cap = std::max<long long>(par.burst_steps, 1);
+    // lattice stencil: mixed precision unless lists are asked for; its own
+    // skin (default 1 A) within the cell edge
+    z->stencil = (par.precision == PTA_PREC_MIXED && par.pair_scheme != PTA_PAIRS_LISTS) ? 1 : 0;
+    z->st_skin = par.stencil_skin > 0.0 ? std::min(par.stencil_skin, par.skin)
+                                        : std::min(1.0, par.skin);
+    z->Lst = std::min(par.lanes ? par.lanes : auto_lanes(z->n, par.precision), 8);
+    z->NKp = s.n_cells[0] + 2 * ST_PK;
+    z->NYp = 2 * s.n_cells[1] + 2 * ST_R;
+    z->NZp = 2 * s.n_cells[2] + 2 * ST_R;
+    z->nslot = z->stencil ? (long long)z->NKp * z->NYp * z->NZp : 0;
+    z->nblk_st = z->stencil ? (int)((z->n * z->Lst + TPB - 1) / TPB) : 0;
     return PTA_OK;
 }
 
 static size_t footprint(const Sizes &z, int prec) {
     const size_t n = (size_t)z.n;
     const size_t p = (prec == PTA_PREC_FP64) ? 32 : 16;
+    const size_t nrec = std::max<size_t>(n, (size_t)z.nslot);  // records: padded for the stencil
     size_t b = 0;
     auto add = [&](size_t x) { b += round_up(x > 0 ? x : 1, 256); };
     add(p * n);
@@ -376,12 +363,12 @@ static size_t footprint(const Sizes &z, int prec) {
     if (prec != PTA_PREC_FP64) {
         add(16 * n);
         add(16 * n);                 // lo[2]
-        add(16 * n);
-        add(16 * n);                 // rel[2]
+        add(16 * nrec);
+        add(16 * nrec);              // rel[2]
         add(n);                      // hsub
     }
-    add(p * n);                      // posfp
-    add(p * n);                      // vel
+    add(p * nrec);                   // posfp
+    add(32 * n);                     // vel (double4 or hi/lo FP32)
     add(n);                          // flags
     add(16 * n);                     // ref
     add(4 * n);                      // atom_cell
@@ -394,19 +381,17 @@ static size_t footprint(const Sizes &z, int prec) {
     add(4 * z.list_words);           // nlist
     if (z.prune_on) {
         add(4 * z.list_words);       // plist
-        add(4 * (size_t)z.nunits * z.L);  // pnn
+        add(4 * n * (size_t)z.L);    // pnn
         add(16 * n);                 // pref
     }
-    add(4 * (size_t)z.nunits);       // nn
-    if (z.tiled) {
-        add(4 * (size_t)z.ntile_grid);             // tile_list
-        add(4 * (size_t)z.ntile_grid * TT_STRIDE); // tile_tab
+    add(4 * n);                      // nn
+    if (z.stencil) {
+        add(4 * n);                    // st_sites
+        add(4 * (size_t)z.nslot);      // st_inv
+        add(16 * 2 * (size_t)ST_TAB);  // st_tab
+        add(4 * (size_t)ST_WORDS);     // st_bits
     }
-    if (z.G == 2) {
-        add(4 * n);                  // unit_first
-        add(4 * ((size_t)z.ncell + 1));  // unit_cell
-    }
-    add(64 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
+    add(64 * (size_t)std::max(std::max(z.nblk_pair, z.nblk_atom), z.nblk_st));  // part
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
     if (z.mean_pos) add(32 * n);     // rsum
@@ -432,14 +417,14 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
     if (par->precision != PTA_PREC_FP64 && par->precision != PTA_PREC_MIXED) return PTA_EINVAL;
     if (par->lanes != 0 && !valid_lanes(par->lanes)) return PTA_EINVAL;
     if (par->atoms_per_thread < 0 || par->atoms_per_thread > 2) return PTA_EINVAL;
-    if (par->atoms_per_thread == 2 &&
-        (par->precision == PTA_PREC_FP64 || (par->lanes != 0 && par->lanes > 2)))
-        return PTA_EUNSUPPORTED;
+    if (par->atoms_per_thread == 2) return PTA_EUNSUPPORTED;
     if (par->neigh_cap < 0 || par->neigh_cap > 4096) return PTA_EINVAL;
     if (par->cell_tiles < -1 || par->cell_tiles > 1) return PTA_EINVAL;
-    if (par->cell_tiles == 1 && (par->precision == PTA_PREC_FP64 || par->atoms_per_thread == 2 ||
-                                 (par->lanes != 0 && par->lanes != 1)))
+    if (par->cell_tiles == 1) return PTA_EUNSUPPORTED;
+    if (par->pair_scheme < PTA_PAIRS_AUTO || par->pair_scheme > PTA_PAIRS_LISTS) return PTA_EINVAL;
+    if (par->pair_scheme == PTA_PAIRS_STENCIL && par->precision == PTA_PREC_FP64)
         return PTA_EUNSUPPORTED;
+    if (!std::isfinite(par->stencil_skin) || par->stencil_skin < 0.0) return PTA_EINVAL;
     if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
     if (par->conv_lag < 0) return PTA_EINVAL;
     if (par->mean_positions != 0 && par->mean_positions != 1) return PTA_EINVAL;
@@ -536,7 +521,12 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
                 rc = PTA_ECUDA;
                 break;
             }
-            if (b == (int)LIST_BUILD) launch_rebuild(r->tab, 0, r->cap2);
+            if (b == (int)LIST_BUILD) {
+                // stencil checks first: a specimen that leaves the stencil
+                // gets its list from the build right behind them
+                launch_stencil_check(r->tab, 0, 0.0, r->cap2);
+                launch_rebuild(r->tab, 0, r->cap2);
+            }
             launch_prune(r->tab, 0, r->cap2);
             cudaGraph_t bout = nullptr;
             if (cudaStreamEndCapture(r->cap2, &bout) != cudaSuccess) rc = PTA_ECUDA;
@@ -569,6 +559,7 @@ static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool t
     CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < iters; ++i) {
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
+        launch_stencil_check(r->tab, 0, 0.0, r->cap);
         launch_rebuild(r->tab, 0, r->cap);
         launch_prune(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
@@ -597,11 +588,24 @@ static int runner_upload(Runner *r) {
     r->hspecs.resize(k);
     int blk_atom = 0, blk_cell = 0;
     std::vector<int> b2s_atom, b2s_cell;
+    // launch groups by (scheme, precision, lanes, potential variant); a
+    // stencil specimen has blocks in a stencil group and in a list group
+    // (the list kernels serve it once it leaves the stencil)
     struct Key {
-        int prec, L, G, sc76, tiled;
+        int prec, L, sc76, scheme;
     };
     std::vector<Key> keys;
     std::vector<std::vector<int>> gb2s;
+    auto group_of = [&](const Key &kk) -> int {
+        for (size_t q = 0; q < keys.size(); ++q)
+            if (keys[q].prec == kk.prec && keys[q].L == kk.L && keys[q].sc76 == kk.sc76 &&
+                keys[q].scheme == kk.scheme)
+                return (int)q;
+        if (keys.size() >= 8) return -1;
+        keys.push_back(kk);
+        gb2s.emplace_back();
+        return (int)keys.size() - 1;
+    };
     for (int i = 0; i < k; ++i) {
         SpecDev s = r->m[i]->hd;
         s.spec_index = i;
@@ -611,19 +615,16 @@ static int runner_upload(Runner *r) {
         s.blk_cell0 = blk_cell;
         blk_cell += s.nblk_cell;
         for (int b = 0; b < s.nblk_cell; ++b) b2s_cell.push_back(i);
-        int g = -1;
-        for (size_t q = 0; q < keys.size(); ++q)
-            if (keys[q].prec == s.prec && keys[q].L == s.L && keys[q].G == s.G &&
-                keys[q].sc76 == s.pot.sc76 && keys[q].tiled == s.tiled)
-                g = (int)q;
-        if (g < 0) {
-            if (keys.size() >= 8) return PTA_EUNSUPPORTED;
-            keys.push_back({s.prec, s.L, s.G, s.pot.sc76, s.tiled});
-            gb2s.emplace_back();
-            g = (int)keys.size() - 1;
-        }
+        int g = group_of({s.prec, s.L, s.pot.sc76, SCHEME_LIST});
+        if (g < 0) return PTA_EUNSUPPORTED;
         s.blk_pair0 = (int)gb2s[g].size();
         for (int b = 0; b < s.nblk_pair; ++b) gb2s[g].push_back(i);
+        if (s.stencil) {
+            g = group_of({s.prec, s.Lst, s.pot.sc76, SCHEME_STENCIL});
+            if (g < 0) return PTA_EUNSUPPORTED;
+            s.blk_st0 = (int)gb2s[g].size();
+            for (int b = 0; b < s.nblk_st; ++b) gb2s[g].push_back(i);
+        }
         r->hspecs[i] = s;
     }
     // one device block for all tables
@@ -674,9 +675,8 @@ static int runner_upload(Runner *r) {
     for (size_t q = 0; q < keys.size(); ++q) {
         t.grp[q].prec = keys[q].prec;
         t.grp[q].L = keys[q].L;
-        t.grp[q].G = keys[q].G;
         t.grp[q].sc76 = keys[q].sc76;
-        t.grp[q].tiled = keys[q].tiled;
+        t.grp[q].scheme = keys[q].scheme;
         t.grp[q].b2s = tabs + off;
         t.grp[q].nblk = (int)gb2s[q].size();
         off += gb2s[q].size();
@@ -982,6 +982,8 @@ int pta_default_params(pta_params *p) {
     p->neigh_cap = 0;
     p->lanes = 0;
     p->cell_tiles = 0;
+    p->pair_scheme = PTA_PAIRS_AUTO;
+    p->stencil_skin = 0.0;
     p->conv_lag = 0;
     p->mean_positions = 0;
     p->conv_tol[0] = p->conv_tol[1] = p->conv_tol[2] = 0.05;
@@ -1015,6 +1017,7 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     const size_t n = (size_t)z.n;
     const bool f64 = c->par.precision == PTA_PREC_FP64;
     const size_t p = f64 ? 32 : 16;
+    const size_t nrec = std::max<size_t>(n, (size_t)z.nslot);
     void *q;
 #define AL(field, bytes, type) \
     CKR(dev_alloc(c, (bytes), &q)); \
@@ -1024,12 +1027,12 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     if (!f64) {
         AL(lo[0], 16 * n, float4 *);
         AL(lo[1], 16 * n, float4 *);
-        AL(rel[0], 16 * n, float4 *);
-        AL(rel[1], 16 * n, float4 *);
+        AL(rel[0], 16 * nrec, float4 *);
+        AL(rel[1], 16 * nrec, float4 *);
         AL(hsub, n, uint8_t *);
     }
-    AL(posfp, p * n, void *);
-    AL(vel, p * n, void *);
+    AL(posfp, p * nrec, void *);
+    AL(vel, 32 * n, void *);
     AL(flags, n, uint8_t *);
     AL(ref, 16 * n, float4 *);
     AL(atom_cell, 4 * n, int *);
@@ -1042,19 +1045,17 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     AL(nlist, 4 * z.list_words, int *);
     if (z.prune_on) {
         AL(plist, 4 * z.list_words, int *);
-        AL(pnn, 4 * (size_t)z.nunits * z.L, int *);
+        AL(pnn, 4 * n * (size_t)z.L, int *);
         AL(pref, 16 * n, float4 *);
     }
-    AL(nn, 4 * (size_t)z.nunits, int *);
-    if (z.tiled) {
-        AL(tile_list, 4 * (size_t)z.ntile_grid, int *);
-        AL(tile_tab, 4 * (size_t)z.ntile_grid * TT_STRIDE, int *);
+    AL(nn, 4 * n, int *);
+    if (z.stencil) {
+        AL(st_sites, 4 * n, int *);
+        AL(st_inv, 4 * (size_t)z.nslot, int *);
+        AL(st_tab, 16 * 2 * (size_t)ST_TAB, int4 *);
+        AL(st_bits, 4 * (size_t)ST_WORDS, unsigned *);
     }
-    if (z.G == 2) {
-        AL(unit_first, 4 * n, int *);
-        AL(unit_cell, 4 * ((size_t)z.ncell + 1), int *);
-    }
-    AL(part, 64 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
+    AL(part, 64 * (size_t)std::max(std::max(z.nblk_pair, z.nblk_atom), z.nblk_st), double *);
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
     if (z.mean_pos) {
@@ -1090,7 +1091,6 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     }
     Sizes z;
     rc = compute_sizes(c->spec, c->pot, c->par, &z);
-    if (rc == PTA_OK && z.tiled && tile_kernels_init() != 0) rc = PTA_ECUDA;
     if (rc != PTA_OK) {
         delete c;
         return rc;
@@ -1099,8 +1099,6 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     std::memset(&s, 0, sizeof(s));
     s.n = (int)z.n;
     s.L = z.L;
-    s.G = z.G;
-    s.nunits = (int)z.nunits;
     s.prec = c->par.precision;
     s.axis = c->spec.load_axis;
     s.cap = z.cap;
@@ -1108,8 +1106,19 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.nblk_pair = z.nblk_pair;
     s.nblk_atom = z.nblk_atom;
     s.nblk_cell = z.nblk_cell;
-    s.tiled = z.tiled;
-    s.ntile_grid = z.ntile_grid;
+    s.stencil = z.stencil;
+    s.Lst = z.Lst;
+    s.nblk_st = z.nblk_st;
+    s.NKp = z.NKp;
+    s.NYp = z.NYp;
+    s.NZp = z.NZp;
+    s.nslot = z.nslot;
+    {
+        const double rs = c->pot.rc + z.st_skin;
+        s.st_rl2 = rs * rs;
+        s.f_st_rl2 = (float)(s.st_rl2 * (1.0 + 1e-5));
+        s.st_half_skin2 = (float)(0.25 * z.st_skin * z.st_skin);
+    }
     for (int d = 0; d < 3; ++d) {
         s.ncl[d] = c->spec.n_cells[d];
         s.org[d] = z.org[d];
@@ -1167,10 +1176,38 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
                             c->stream) != cudaSuccess)
             rc = PTA_ECUDA;
     }
+    // stencil: the brick order of the atoms (site of every slot, packed
+    // k | Y << 10 | Z << 20) and its inverse over the padded record slots
+    std::vector<int> st_sites, st_inv;
+    if (rc == PTA_OK && s.stencil) {
+        const int nx = c->spec.n_cells[0], ny2 = 2 * c->spec.n_cells[1],
+                  nz2 = 2 * c->spec.n_cells[2];
+        st_sites.reserve((size_t)s.n);
+        st_inv.assign((size_t)s.nslot, -1);
+        for (int bz = 0; bz < nz2; bz += ST_BZ)
+            for (int by = 0; by < ny2; by += ST_BY)
+                for (int bk = 0; bk < nx; bk += ST_BK)
+                    for (int Z = bz; Z < std::min(bz + ST_BZ, nz2); ++Z)
+                        for (int Y = by; Y < std::min(by + ST_BY, ny2); ++Y)
+                            for (int k = bk; k < std::min(bk + ST_BK, nx); ++k) {
+                                const long long ps =
+                                    ((long long)(Z + ST_R) * s.NYp + (Y + ST_R)) * s.NKp + k + ST_PK;
+                                st_inv[(size_t)ps] = (int)st_sites.size();
+                                st_sites.push_back(k | (Y << 10) | (Z << 20));
+                            }
+        if ((long long)st_sites.size() != s.n ||
+            cudaMemcpyAsync(s.st_sites, st_sites.data(), 4 * st_sites.size(),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(s.st_inv, st_inv.data(), 4 * st_inv.size(), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess)
+            rc = PTA_ECUDA;
+    }
     if (rc == PTA_OK) {
         const double kT = kb_ev() * T0;
         const double sigma = std::sqrt(kT / (s.mass * mv2_to_ev()));
         launch_create(c->hd, c->d_self, sigma, kT, seed, c->stream);
+        // the stencil keeps atoms in lattice row order from the start
+        if (s.stencil) launch_stencil_order(c->hd, c->d_self, c->stream);
         launch_import(c->hd, c->d_self, c->stream);
         rc = launch_check();
     }
@@ -1216,30 +1253,22 @@ static int fetch_orig(pta_ctx *c, std::vector<int> &orig) {
 int pta_get_layout(const pta_ctx *c, int32_t out[4]) {
     if (!c || !out) return PTA_EINVAL;
     out[0] = c->hd.L;
-    out[1] = c->hd.G;
+    out[1] = 1;
     out[2] = c->hd.cap_use;
     out[3] = c->hd.prune_on;
     return PTA_OK;
 }
 
-int pta_get_tiling(pta_ctx *c, int32_t out[4]) {
+int pta_get_scheme(pta_ctx *c, int32_t out[4]) {
     if (!c || !out) return PTA_EINVAL;
-    for (int q = 0; q < 4; ++q) out[q] = 0;
-    out[0] = c->hd.tiled;
-    if (!c->hd.tiled) return PTA_OK;
     if (c->broken) return PTA_ECUDA;
-    out[1] = c->hd.nblk_pair;
     SpecCtl ctl;
-    std::vector<int> tab((size_t)c->hd.ntile_grid * TT_STRIDE), list((size_t)c->hd.ntile_grid);
     CK(cudaMemcpyAsync(&ctl, c->hd.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(tab.data(), c->hd.tile_tab, 4 * tab.size(), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaMemcpyAsync(list.data(), c->hd.tile_list, 4 * list.size(), cudaMemcpyDeviceToHost,
-                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    out[2] = ctl.ntiles;
-    for (int k = 0; k < ctl.ntiles && k < (int)list.size(); ++k)
-        out[3] += tab[(size_t)list[k] * TT_STRIDE + TT_STAGED] != 0;
+    out[0] = ctl.scheme == SCHEME_STENCIL ? PTA_PAIRS_STENCIL : PTA_PAIRS_LISTS;
+    out[1] = ctl.scheme == SCHEME_STENCIL ? ctl.nkey : 0;
+    out[2] = ctl.st_checks;
+    out[3] = c->hd.stencil ? c->hd.Lst : 0;
     return PTA_OK;
 }
 
@@ -1423,6 +1452,7 @@ int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     if (!c || n != c->hd.n) return PTA_EINVAL;
     Runner *r;
     CKR(ctx_solo(c, &r));
+    launch_stencil_check(r->tab, 1, 0.0, c->stream);
     launch_rebuild(r->tab, 1, c->stream);
     launch_prune(r->tab, 1, c->stream);
     launch_density(r->tab, 1, c->stream);
@@ -1453,81 +1483,48 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     if (!c || n != c->hd.n || !max_count) return PTA_EINVAL;
     Runner *r;
     CKR(ctx_solo(c, &r));
-    launch_rebuild(r->tab, 1, c->stream);
-    CKR(launch_check());
     const SpecDev &s = c->hd;
-    std::vector<int> nn((size_t)s.nunits), raw;
     SpecCtl ctl;
-    CK(cudaMemcpyAsync(nn.data(), s.nn, 4 * (size_t)s.nunits, cudaMemcpyDeviceToHost, c->stream));
+    bool st = false;
+    if (s.stencil) {
+        // the stencil checked at the list radius, then its pairs within that
+        // radius (a check that leaves the stencil falls back to the lists)
+        launch_stencil_check(r->tab, 1, s.rl2, c->stream);
+        CKR(launch_check());
+        CK(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        st = ctl.scheme == SCHEME_STENCIL;
+    }
+    if (st) {
+        CK(cudaMemsetAsync(&s.ctl->max_nn, 0, sizeof(int), c->stream));
+        launch_stencil_list(c->hd, c->d_self, c->stream);
+    } else {
+        launch_rebuild(r->tab, 1, c->stream);
+    }
+    CKR(launch_check());
+    const int L = st ? 1 : s.L;
+    std::vector<int> nn((size_t)n), raw;
+    CK(cudaMemcpyAsync(nn.data(), s.nn, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-    const long long W = 32 / s.L;
-    const size_t words = (size_t)((s.nunits + W - 1) / W) * W * s.cap;
+    const long long W = 32 / L;
+    const size_t words = (size_t)((n + W - 1) / W) * W * s.cap;
     raw.resize(words);
     std::vector<int> orig;
     CK(cudaMemcpyAsync(raw.data(), s.nlist, 4 * words, cudaMemcpyDeviceToHost, c->stream));
     CKR(fetch_orig(c, orig));
-    // exact positions in slot order, for splitting a unit's union list
-    std::vector<double> pos;
-    if (s.G > 1) {
-        launch_export(c->hd, c->d_self, c->stream);
-        CKR(launch_check());
-        pos.resize(3 * (size_t)n);
-        CK(cudaMemcpyAsync(pos.data(), s.stage, 24 * (size_t)n, cudaMemcpyDeviceToHost,
-                           c->stream));
-    }
     CK(cudaStreamSynchronize(c->stream));
     *max_count = ctl.max_nn;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
-    // tiled: entries of a staged tile are slots of its halo copy; map them
-    // back through the tile table (stage offset and first slot of each halo cell)
-    std::vector<int> ttab, acell;
-    if (s.tiled) {
-        ttab.resize((size_t)s.ntile_grid * TT_STRIDE);
-        acell.resize((size_t)n);
-        CK(cudaMemcpy(ttab.data(), s.tile_tab, 4 * ttab.size(), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(acell.data(), s.atom_cell, 4 * (size_t)n, cudaMemcpyDeviceToHost));
-    }
-    std::vector<int> ufirst;
-    if (s.G == 2) {
-        ufirst.resize((size_t)ctl.nunits);
-        CK(cudaMemcpy(ufirst.data(), s.unit_first, 4 * (size_t)ctl.nunits, cudaMemcpyDeviceToHost));
-    }
-    std::vector<int> row;
     int maxc = 0;
-    for (int64_t u = 0; u < ctl.nunits; ++u) {
-        int a0 = (int)u, ga = 1;
-        if (s.G == 2) {
-            a0 = ufirst[u] & (UNIT_SECOND - 1);
-            ga = (ufirst[u] & UNIT_SECOND) ? 2 : 1;
-        }
-        for (int g = 0; g < ga; ++g) {
-            const int64_t a = a0 + g;
-            row.clear();
-            const int *T = s.tiled ? &ttab[(size_t)(acell[a] >> 3) * TT_STRIDE] : nullptr;
-            for (int k = 0; k < nn[u]; ++k) {
-                int j = nl_j((unsigned)raw[(size_t)nl_index((int)u, k, s.L, s.cap)]);
-                if (T && T[TT_STAGED]) {
-                    const int *off = T + TT_OFF;
-                    const int hc = (int)(std::upper_bound(off, off + TILE_HALO + 1, j) - off) - 1;
-                    if (hc < 0 || hc >= TILE_HALO || j >= off[TILE_HALO]) return PTA_ECUDA;
-                    j = T[TT_START + hc] + (j - off[hc]);
-                }
-                if (j < 0 || j >= n) return PTA_ECUDA;
-                if (s.G > 1) {
-                    // the same FP64 predicate as the list build (no contraction)
-                    if (j == a) continue;
-                    const double *pa = &pos[3 * (size_t)orig[a]], *pj = &pos[3 * (size_t)orig[j]];
-                    const double dx = pj[0] - pa[0], dy = pj[1] - pa[1], dz = pj[2] - pa[2];
-                    if (!((dx * dx + dy * dy) + dz * dz < s.rl2)) continue;
-                }
-                row.push_back(orig[j]);
-            }
-            maxc = std::max<int>(maxc, (int)row.size());
-            const int64_t o = orig[a];
-            if (counts) counts[o] = (int32_t)row.size();
-            if ((int)row.size() > cap) return PTA_EINVAL;
-            if (list)
-                for (size_t k = 0; k < row.size(); ++k) list[o * (int64_t)cap + k] = row[k];
+    for (int64_t u = 0; u < n; ++u) {
+        const int64_t o = orig[u];
+        if (counts) counts[o] = nn[u];
+        maxc = std::max(maxc, nn[u]);
+        if (nn[u] > cap) return PTA_EINVAL;
+        for (int k = 0; k < nn[u]; ++k) {
+            const int j = nl_j((unsigned)raw[(size_t)nl_index((int)u, k, L, s.cap)]);
+            if (j < 0 || j >= n) return PTA_ECUDA;
+            if (list) list[o * (int64_t)cap + k] = orig[j];
         }
     }
     *max_count = maxc;
@@ -1535,7 +1532,8 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
 }
 
 // checkpoint layout: header, PtaDev, then the raw working arrays of the
-// current position buffer and the velocities
+// current position buffer, the velocities and the grip flags, in creation
+// order (independent of the slot order the pair scheme keeps)
 struct CkptHeader {
     char magic[8];
     int32_t version, prec;
@@ -1547,7 +1545,7 @@ struct CkptHeader {
 static size_t ckpt_payload(const pta_ctx *c) {
     const size_t n = (size_t)c->hd.n;
     const size_t p = (c->hd.prec == PTA_PREC_FP64) ? 32 : 16;
-    return p * n * 2 + (c->hd.prec == PTA_PREC_FP64 ? 0 : 16 * n) + n + 4 * n;
+    return p * n + (c->hd.prec == PTA_PREC_FP64 ? 0 : 16 * n) + 32 * n + n;
 }
 
 int pta_save_state(pta_ctx *c, void *buf, size_t *len) {
@@ -1561,10 +1559,11 @@ int pta_save_state(pta_ctx *c, void *buf, size_t *len) {
     if (*len < need) return PTA_EINVAL;
     SpecCtl ctl;
     CK(cudaMemcpyAsync(&ctl, c->hd.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    launch_ckpt_move(c->hd, c->d_self, 1, c->stream);
+    CKR(launch_check());
     CkptHeader h{};
     std::memcpy(h.magic, "PTACKPT", 8);
-    h.version = 1;
+    h.version = 2;
     h.prec = c->hd.prec;
     h.n = c->hd.n;
     h.u = c->u;
@@ -1573,23 +1572,22 @@ int pta_save_state(pta_ctx *c, void *buf, size_t *len) {
     char *o = (char *)buf;
     std::memcpy(o, &h, sizeof(h));
     o += sizeof(h);
-    std::memcpy(o, &ctl.pta, sizeof(PtaDev));
-    o += sizeof(PtaDev);
     const size_t n = (size_t)c->hd.n;
     const size_t p = (c->hd.prec == PTA_PREC_FP64) ? 32 : 16;
-    const int par = ctl.parity;
-    CK(cudaMemcpyAsync(o, c->hd.pos[par], p * n, cudaMemcpyDeviceToHost, c->stream));
-    o += p * n;
-    CK(cudaMemcpyAsync(o, c->hd.vel, p * n, cudaMemcpyDeviceToHost, c->stream));
-    o += p * n;
+    const PermLayout Lo = perm_layout(n, c->hd.prec);
+    const char *t = (const char *)c->hd.perm_tmp;
+    char *pl = o + sizeof(PtaDev);
+    CK(cudaMemcpyAsync(pl, t + Lo.pos, p * n, cudaMemcpyDeviceToHost, c->stream));
+    pl += p * n;
     if (c->hd.prec != PTA_PREC_FP64) {
-        CK(cudaMemcpyAsync(o, c->hd.lo[par], 16 * n, cudaMemcpyDeviceToHost, c->stream));
-        o += 16 * n;
+        CK(cudaMemcpyAsync(pl, t + Lo.lo, 16 * n, cudaMemcpyDeviceToHost, c->stream));
+        pl += 16 * n;
     }
-    CK(cudaMemcpyAsync(o, c->hd.flags, n, cudaMemcpyDeviceToHost, c->stream));
-    o += n;
-    CK(cudaMemcpyAsync(o, c->hd.orig, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(pl, t + Lo.vel, 32 * n, cudaMemcpyDeviceToHost, c->stream));
+    pl += 32 * n;
+    CK(cudaMemcpyAsync(pl, t + Lo.flags, n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(o, &ctl.pta, sizeof(PtaDev));
     *len = need;
     return PTA_OK;
 }
@@ -1601,7 +1599,7 @@ int pta_load_state(pta_ctx *c, const void *buf, size_t len) {
     if (len < need) return PTA_EINVAL;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "PTACKPT", 8) != 0 || h.version != 1 || h.prec != c->hd.prec ||
+    if (std::memcmp(h.magic, "PTACKPT", 8) != 0 || h.version != 2 || h.prec != c->hd.prec ||
         h.n != c->hd.n)
         return PTA_EINVAL;
     const char *o = (const char *)buf + sizeof(h);
@@ -1615,19 +1613,20 @@ int pta_load_state(pta_ctx *c, const void *buf, size_t len) {
     ctl.blocks_done = 0;
     const size_t n = (size_t)c->hd.n;
     const size_t p = (c->hd.prec == PTA_PREC_FP64) ? 32 : 16;
-    const int par = ctl.parity;
-    CK(cudaMemcpyAsync(c->hd.pos[par], o, p * n, cudaMemcpyHostToDevice, c->stream));
-    o += p * n;
-    CK(cudaMemcpyAsync(c->hd.vel, o, p * n, cudaMemcpyHostToDevice, c->stream));
+    const PermLayout Lo = perm_layout(n, c->hd.prec);
+    char *t = (char *)c->hd.perm_tmp;
+    CK(cudaMemcpyAsync(t + Lo.pos, o, p * n, cudaMemcpyHostToDevice, c->stream));
     o += p * n;
     if (c->hd.prec != PTA_PREC_FP64) {
-        CK(cudaMemcpyAsync(c->hd.lo[par], o, 16 * n, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(t + Lo.lo, o, 16 * n, cudaMemcpyHostToDevice, c->stream));
         o += 16 * n;
     }
-    CK(cudaMemcpyAsync(c->hd.flags, o, n, cudaMemcpyHostToDevice, c->stream));
-    o += n;
-    CK(cudaMemcpyAsync(c->hd.orig, o, 4 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(t + Lo.vel, o, 32 * n, cudaMemcpyHostToDevice, c->stream));
+    o += 32 * n;
+    CK(cudaMemcpyAsync(t + Lo.flags, o, n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->hd.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, c->stream));
+    launch_ckpt_move(c->hd, c->d_self, 0, c->stream);
+    CKR(launch_check());
     CK(cudaStreamSynchronize(c->stream));
     c->u = h.u;
     c->pta_init = h.pta_init != 0;

@@ -20,20 +20,6 @@ constexpr int CELL_WARPS = 8;   // warps per block of the cell-sort kernel
 constexpr int CELLS_PER_WARP = 8;  // cells one warp of the cell-sort kernel orders in turn
 constexpr int SCAN_THREADS = 1024;
 
-// Cell tiles of the mixed-precision, one-lane-per-atom pair passes: a block
-// takes a tile of 2x2x2 cells; every neighbour of its atoms lies in the
-// 4x4x4 cells around it (the tile's halo, cells numbered hx + 4 hy + 16 hz).
-// When the halo holds at most TILE_SC atoms their records are copied into
-// shared memory and the tile's list entries index that copy.
-constexpr int TILE_T = 384;      // threads per block of the tile kernels
-constexpr int TILE_SC = 3328;    // records a staged halo may hold (52 KB)
-constexpr int TILE_HALO = 64;
-// per-tile table (ints): first atom, end atom, staged flag, stage offset of
-// each halo cell (65 entries, the last = halo atoms), first slot of each
-// halo cell (64)
-constexpr int TT_A0 = 0, TT_A1 = 1, TT_STAGED = 2, TT_OFF = 3, TT_START = TT_OFF + TILE_HALO + 1;
-constexpr int TT_STRIDE = TT_START + TILE_HALO;  // 132
-
 // grid quantum of the mixed-precision position split x = hi + lo:
 // hi is a multiple of 2^-12 A (exact in FP32 for |x| < 512 A), |lo| <= 2^-13 A
 constexpr double HI_SCALE = 4096.0;
@@ -42,6 +28,36 @@ constexpr double MIXED_RANGE = 511.0;
 
 enum Phase : int { PH_IDLE = 0, PH_REFRESH = 1, PH_RUN = 2 };
 enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4 };
+// how a specimen's pair passes find neighbours: Verlet lists, or the lattice
+// stencil (mixed precision; a specimen leaves the stencil for lists on the
+// device once its neighbour pairs no longer fit the stencil's range)
+enum Scheme : int { SCHEME_LIST = 0, SCHEME_STENCIL = 1 };
+
+// Atoms of a stencil specimen are kept in brick order: bricks of ST_BK sites
+// along a row x ST_BY rows along y x ST_BZ rows along z, bricks in (z, y, x)
+// order, sites within a brick in (z, y, x) order, so that a thread block's
+// atoms form a compact block of the crystal (its neighbours' records stay in
+// L1) while a warp still reads runs of ST_BK consecutive records.
+constexpr int ST_BK = 8, ST_BY = 4, ST_BZ = 4;
+
+// Lattice stencil (k_stencil.cu): lattice vectors in units of a0 / 2 with
+// every component in [-ST_R, ST_R]; at most ST_KEYS of them; the padded
+// record arrays extend ST_PK sites along each row and ST_R rows along y and z
+// beyond the lattice, so that every stencil neighbour of a lattice site has
+// a slot
+constexpr int ST_R = 10;
+constexpr int ST_SIDE = 2 * ST_R + 1;
+constexpr int ST_BITS = ST_SIDE * ST_SIDE * ST_SIDE;
+constexpr int ST_WORDS = (ST_BITS + 31) / 32;
+constexpr int ST_KEYS = 1024;
+constexpr int ST_TAB = ST_KEYS + 64;  // entries per parity table (spare far entries at the end)
+constexpr int ST_PK = (ST_R + 1) / 2;
+constexpr float ST_FAR = 1.0e4f;      // coordinate of the records of empty slots (A)
+
+// mixed precision: velocity as an exact FP32 pair v = h + l
+struct __align__(32) VelHL {
+    float4 h, l;
+};
 enum Mode : int { MODE_STEP = 0, MODE_EVAL = 1 };
 enum AtomFlag : uint8_t { FLAG_MOBILE = 0, FLAG_LEFT = 1, FLAG_RIGHT = 2 };
 
@@ -73,10 +89,14 @@ struct SpecCtl {
     int list_L;                // lanes the current list layout was built for
     int rebuilds;              // list builds in the current burst
     int max_nn;                // largest neighbour count at the last build
-    int nunits;                // units in use (G = 2: pairs of atoms of one cell)
     int prune;                 // 1: prune the inner list before the next pair pass
     int prunes;                // prunings in the current burst
-    int ntiles;                // occupied cell tiles at the last build
+    int scheme;                // Scheme of the pair passes (stencil specimens may fall back)
+    int nkey;                  // stencil: keys in the current table (a multiple of 4)
+    int st_err;                // stencil: the last check found pairs beyond its range or cap
+    int st_checks;             // stencil: checks since creation
+    int st_box[6];             // stencil: per-axis min and max of the positions (ordered ints)
+    float st_q[3], st_o[3];    // stencil: reference lattice, site = o + (X q_x, Y q_y, Z q_z)
     double sum[3];             // running sums of K, U, T over the burst (in step order)
     double sum_chk[3];         // adaptive length: running sums at the last check
     double conv_val[3];        // adaptive length: running average at convergence
@@ -93,14 +113,20 @@ struct SpecDev {
     // sizes
     int n, L, prec, axis, cap;   // cap: list stride per unit (usable entries: cap_use)
     int cap_use;
-    int G, nunits;             // atoms per unit (one thread group and one list per unit);
-                               // nunits is the capacity (units in use: SpecCtl::nunits)
-    int blk_pair0, nblk_pair;  // pair kernels: TPB/L units per block
+    int blk_pair0, nblk_pair;  // list pair kernels: TPB/L atoms per block
+    int blk_st0, nblk_st, Lst; // stencil pair kernels: TPB/Lst atoms per block, Lst lanes each
     int blk_atom0, nblk_atom;  // one thread per atom
     int blk_cell0, nblk_cell;  // cell sort: CELLS_PER_WARP cells per warp
     int spec_index;            // index of this specimen in the launch table
-    int tiled;                 // pair passes by cell tiles (nblk_pair blocks loop over them)
-    int ntile_grid;            // tiles of the cell grid (ncell / 8)
+    // stencil geometry: rows of ncl[0] sites along x for every (Y, Z) in
+    // [0, 2 ncl[1]) x [0, 2 ncl[2]) (half lattice units); padded slot of
+    // site (k, Y, Z) = ((Z + ST_R) NYp + Y + ST_R) NKp + k + ST_PK
+    int stencil;               // 1: the specimen may use the stencil
+    int NKp, NYp, NZp;
+    long long nslot;           // NKp NYp NZp
+    double st_rl2;             // squared radius the stencil must cover (rc + stencil skin)^2
+    float f_st_rl2;            // its FP32 value widened by 1e-5 (the check's test)
+    float st_half_skin2;       // (stencil skin / 2)^2: a check is due beyond this displacement
     // lattice (creation only)
     int ncl[3];
     double a0, grip_width;
@@ -132,15 +158,16 @@ struct SpecDev {
                     // (FP32): the 16-byte record the pair passes read for a neighbour
     uint8_t *hsub;  // MIXED only: half-cell of each atom in its cell (bit d: upper half
                     // along axis d), fixed from one list build to the next
-    void *vel;      // FP64: double4; MIXED: float4
+    void *vel;      // FP64: double4; MIXED: VelHL
     uint8_t *flags;
     float4 *ref;    // positions at the last list build (skin test)
     int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
     int *orig;        // original index (creation order) of the atom stored at each slot
-    int *tile_list;   // tiled: occupied tiles in rank order (SpecCtl::ntiles of them)
-    int *tile_tab;    // tiled: TT_STRIDE ints per tile of the grid
-    int *unit_first;  // G = 2: first slot of each unit | (1 << 30) when it has a second atom
-    int *unit_cell;   // G = 2: first unit of each cell (ncell + 1)
+    int *st_sites;    // stencil: site of every atom slot, k | Y << 10 | Z << 20
+    int *st_inv;      // stencil: atom slot of every padded record slot (-1: none)
+    int4 *st_tab;     // stencil: two tables of ST_TAB entries (even, odd rows):
+                      // {slot offset, c_x, c_y, c_z (float bits)} per key
+    unsigned *st_bits;  // stencil: ST_WORDS words, the keys seen by the check
     void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
     int *nlist, *nn;
     int *plist, *pnn;   // inner list (same layout as nlist), entries per unit and lane
@@ -158,7 +185,7 @@ struct SpecDev {
 };
 
 struct Group {
-    int prec, L, G, sc76, tiled;
+    int prec, L, sc76, scheme;
     const int *b2s;
     int nblk;
 };
@@ -207,10 +234,7 @@ __device__ __forceinline__ float nl_offz(unsigned e) {
 // Cells are numbered along a serpentine path (x reverses on every other row,
 // y on every other layer), so that consecutive cells are face neighbours and
 // consecutive atoms of the cell-sorted order lie in the same or adjacent
-// cells.  With cell tiles (tm = 1) the same path runs over tiles of 2x2x2
-// cells (the grid has an even number of cells per axis) and the 8 cells of
-// tile t take ranks 8t + (x & 1) + 2 (y & 1) + 4 (z & 1), so that a tile's
-// atoms are one contiguous range.
+// cells.
 __host__ __device__ __forceinline__ int serp_rank(int n0, int n1, int x, int y, int z) {
     const int yr = (z & 1) ? n1 - 1 - y : y;
     const int t = z * n1 + yr;
@@ -224,34 +248,18 @@ __host__ __device__ __forceinline__ void serp_coords(int n0, int n1, int r, int 
     y = (z & 1) ? n1 - 1 - yr : yr;
     x = (t & 1) ? n0 - 1 - xr : xr;
 }
-__host__ __device__ __forceinline__ int cell_rank(int tm, const int nc[3], int x, int y, int z) {
-    if (!tm) return serp_rank(nc[0], nc[1], x, y, z);
-    return (serp_rank(nc[0] >> 1, nc[1] >> 1, x >> 1, y >> 1, z >> 1) << 3) | (x & 1) |
-           ((y & 1) << 1) | ((z & 1) << 2);
+__host__ __device__ __forceinline__ int cell_rank(const int nc[3], int x, int y, int z) {
+    return serp_rank(nc[0], nc[1], x, y, z);
 }
-// tile coordinates of tile rank b (tile-major numbering)
-__host__ __device__ __forceinline__ void tile_coords(const int nc[3], int b, int &bx, int &by,
-                                                     int &bz) {
-    serp_coords(nc[0] >> 1, nc[1] >> 1, b, bx, by, bz);
-}
-__host__ __device__ __forceinline__ void cell_coords(int tm, const int nc[3], int r, int &x, int &y,
-                                                     int &z) {
-    if (!tm) {
-        serp_coords(nc[0], nc[1], r, x, y, z);
-        return;
-    }
-    int bx, by, bz;
-    tile_coords(nc, r >> 3, bx, by, bz);
-    x = 2 * bx + (r & 1);
-    y = 2 * by + ((r >> 1) & 1);
-    z = 2 * bz + ((r >> 2) & 1);
+__host__ __device__ __forceinline__ void cell_coords(const int nc[3], int r, int &x, int &y, int &z) {
+    serp_coords(nc[0], nc[1], r, x, y, z);
 }
 
 // centre of the cell of rank r (exact in FP32: org on a 2^-12 grid, h a
 // multiple of 2^-11)
 __device__ __forceinline__ float3 cell_centre(const SpecDev &S, int r) {
     int cx, cy, cz;
-    cell_coords(S.tiled, S.nc, r, cx, cy, cz);
+    cell_coords(S.nc, r, cx, cy, cz);
     return make_float3(S.f_org[0] + ((float)cx + 0.5f) * S.f_h,
                        S.f_org[1] + ((float)cy + 0.5f) * S.f_h,
                        S.f_org[2] + ((float)cz + 0.5f) * S.f_h);
@@ -286,7 +294,7 @@ __host__ __device__ inline PermLayout perm_layout(size_t n, int prec) {
     L.lo = o;
     o += prec == PTA_PREC_FP64 ? 0 : perm_round(16 * n);
     L.vel = o;
-    o += perm_round(P * n);
+    o += perm_round(32 * n);  // double4 or VelHL
     L.flags = o;
     o += perm_round(n);
     L.orig = o;
@@ -295,19 +303,6 @@ __host__ __device__ inline PermLayout perm_layout(size_t n, int prec) {
     o += perm_round(4 * n);
     L.total = o;
     return L;
-}
-
-// atoms of unit u: first slot and count (G = 1: the unit is the atom)
-constexpr int UNIT_SECOND = 1 << 30;
-__device__ __forceinline__ void unit_atoms(const SpecDev &S, int u, int &a0, int &ga) {
-    if (S.G == 1) {
-        a0 = u;
-        ga = 1;
-    } else {
-        const int info = S.unit_first[u];
-        a0 = info & (UNIT_SECOND - 1);
-        ga = (info & UNIT_SECOND) ? 2 : 1;
-    }
 }
 
 // Rows of a warp's list tile (L = 1: row k holds entry k of the warp's 32
@@ -347,6 +342,51 @@ __host__ __device__ __forceinline__ long long nl_index(int a, int k, int L, int 
     return nl_base(a, L, cap) + (long long)(k / L) * 32 + (k % L);
 }
 
+// one block of SCAN_THREADS threads per specimen: exclusive scan of the cell
+// counts into cell_start (cell_start[ncell] = total); the counts are reset to
+// 0 for use as fill counters by a scatter; the specimen's build count + 1
+__device__ __forceinline__ void scan_cells(const SpecDev &S) {
+    __shared__ int wsum[SCAN_THREADS / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < S.ncell; base += SCAN_THREADS) {
+        const int c = base + threadIdx.x;
+        const int v = (c < S.ncell) ? S.cell_cnt[c] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
+        if (c < S.ncell) {
+            S.cell_start[c] = excl;
+            S.cell_cnt[c] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        S.cell_start[S.ncell] = carry;
+        S.ctl->rebuilds += 1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -356,6 +396,8 @@ void launch_create(const SpecDev &h, const SpecDev *d, double sigma_v, double kT
 void launch_import(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_export(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_fix_right_grip(const SpecDev &h, const SpecDev *d, cudaStream_t st);
+// checkpoints: working state <-> permutation scratch in creation order
+void launch_ckpt_move(const SpecDev &h, const SpecDev *d, int gather, cudaStream_t st);
 // batched
 void launch_strain(const Tab &t, const double *du, cudaStream_t st);
 void launch_burst_begin(const Tab &t, const long long *nsteps, cudaStream_t st);
@@ -364,6 +406,13 @@ void launch_any_running(const Tab &t, int *flag, cudaStream_t st);
 void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
 void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
 void launch_rebuild(const Tab &t, int force, cudaStream_t st);
+// stencil: check the pairs within the stencil radius (rl2_override > 0: that
+// radius instead) and rebuild the key table; set up the row order at creation
+void launch_stencil_check(const Tab &t, int force, double rl2_override, cudaStream_t st);
+void launch_stencil_order(const SpecDev &h, const SpecDev *d, cudaStream_t st);
+// stencil: write each atom's stencil neighbours within sqrt(rl2) into the
+// Verlet-list arrays (FP64 predicate), for pta_get_neighbours
+void launch_stencil_list(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_prune(const Tab &t, int force, cudaStream_t st);
 void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st);
 // list maintenance decided on the device: 0 build + prune, 1 prune, 2 nothing
@@ -375,7 +424,6 @@ __device__ __forceinline__ bool prune_active(const SpecDev &S, int force) {
     return S.ctl->phase != PH_IDLE && S.ctl->prune != 0;
 }
 void launch_density(const Tab &t, int force, cudaStream_t st);
-int tile_kernels_init();  // 0 when the tile kernels can use their shared memory
 void launch_force(const Tab &t, int mode, cudaStream_t st);
 
 }  // namespace pta
