@@ -467,8 +467,7 @@ def run_pta(args, wl):
     # density and force passes; per list build 12 kernels; per pruning one
     # kernel per group and one bookkeeping kernel; per burst the grip
     # increment, burst start and burst end; per coarse step the update
-    groups = len({(c.params.precision, c.layout()["lanes"], c.scheme()["scheme"])
-                  for c in ctxs})
+    groups = len({(c.params.precision, c.layout()["lanes"]) for c in ctxs})
     builds = sum(b.rebuilds for step in results for r in step for b in r.burst)
     prunes = sum(b.prunes for step in results for r in step for b in r.burst)
     bursts = 3 * args.steps

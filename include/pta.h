@@ -71,22 +71,7 @@ typedef enum {
 enum { PTA_POT_SUTTON_CHEN_SF = 1 };
 enum { PTA_PREC_FP64 = 0, PTA_PREC_MIXED = 1 };
 enum { PTA_SRC_PREDICTED = 0, PTA_SRC_MEASURE_JUMP = 1, PTA_SRC_MEASURE_MISMATCH = 2 };
-/* How the pair passes of Eqs. (pe) and (f_int) find each atom's neighbours.
- *   PTA_PAIRS_LISTS: Verlet lists (cell binning by counting sort, a list of
- *     every pair within rc + skin, rebuilt when an atom has moved skin / 2).
- *   PTA_PAIRS_STENCIL (mixed precision): the lattice stencil.  The specimen
- *     is a crystal built site by site, and while it keeps its lattice the
- *     neighbour at lattice offset v of every atom is the atom at that
- *     offset; atoms stay in lattice row order and the pair passes visit, for
- *     every atom, the same set of offsets (every offset of a pair within
- *     rc + stencil_skin at the last check; a check runs whenever an atom has
- *     moved stencil_skin / 2, and at every burst start).  Pairs beyond rc
- *     contribute nothing, so the sums are those of the equations, in another
- *     order.  When a check finds offsets too wide or too many for the
- *     stencil (the crystal has slipped), the specimen moves to Verlet lists
- *     on the device before the next pair pass, and stays there.
- *   PTA_PAIRS_AUTO: the stencil for mixed precision, lists for FP64. */
-enum { PTA_PAIRS_AUTO = 0, PTA_PAIRS_STENCIL = 1, PTA_PAIRS_LISTS = 2 };
+
 
 /* Specimen (problem-setup section; grips from the boundary-conditions
  * section).  n_cells >= 3 along the load axis and >= 1 along the others.
@@ -152,10 +137,6 @@ typedef struct {
     int mean_positions; /* 1: also average every atom's position over the
                            states a burst samples (Eq. (mean_pos)), read with
                            pta_get_mean_positions; 0 (default) = off        */
-    int pair_scheme;    /* PTA_PAIRS_AUTO (default), _STENCIL (mixed precision
-                           only, else PTA_EUNSUPPORTED) or _LISTS            */
-    double stencil_skin;/* skin of the lattice stencil, A (0 = default 1 A;
-                           at most skin)                                     */
 } pta_params;
 
 /* Burst result: Eq. (R_m_t) means over the nsteps samples taken after each
@@ -238,12 +219,6 @@ int pta_natoms(const pta_ctx *ctx, int64_t *n);
  * (lanes), out[1] atoms per thread group, out[2] neighbour-list capacity per
  * atom, out[3] 1 when the pruned inner list is in use. */
 int pta_get_layout(const pta_ctx *ctx, int32_t out[4]);
-/* The pair scheme of this context now: out[0] PTA_PAIRS_STENCIL or
- * PTA_PAIRS_LISTS (a stencil context that has left the stencil reports
- * lists), out[1] lattice offsets in the stencil (0 on lists), out[2] stencil
- * checks since creation, out[3] threads per atom of the stencil kernels (0
- * when the context cannot use the stencil). */
-int pta_get_scheme(pta_ctx *ctx, int32_t out[4]);
 /* 0 mobile, 1 left grip, 2 right grip; n must equal the atom count */
 int pta_get_flags(pta_ctx *ctx, uint8_t *flags, int64_t n);
 

@@ -34,7 +34,6 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpta.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
-PAIRS_AUTO, PAIRS_STENCIL, PAIRS_LISTS = 0, 1, 2
 SRC_PREDICTED, SRC_MEASURE_JUMP, SRC_MEASURE_MISMATCH = 0, 1, 2
 
 _STATUS = {0: "PTA_OK", -1: "PTA_EINVAL", -2: "PTA_ENOMEM", -3: "PTA_ECUDA",
@@ -72,8 +71,7 @@ class Params(ctypes.Structure):
                 ("lanes", ctypes.c_int), ("atoms_per_thread", ctypes.c_int),
                 ("prune_margin", ctypes.c_double), ("cell_tiles", ctypes.c_int),
                 ("conv_lag", ctypes.c_int), ("conv_tol", ctypes.c_double * 3),
-                ("mean_positions", ctypes.c_int), ("pair_scheme", ctypes.c_int),
-                ("stencil_skin", ctypes.c_double)]
+                ("mean_positions", ctypes.c_int)]
 
 
 class Averages(ctypes.Structure):
@@ -126,7 +124,6 @@ _SIGS = {
     "pta_destroy": (None, [_VP]),
     "pta_natoms": (ctypes.c_int, [_VP, _P(ctypes.c_int64)]),
     "pta_get_layout": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
-    "pta_get_scheme": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
     "pta_get_mean_positions": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64]),
     "pta_relax": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                  _P(Averages), _P(ctypes.c_int64)]),
@@ -290,13 +287,6 @@ def pta_get_layout(h) -> dict:
     _check(load().pta_get_layout(h, out), "pta_get_layout")
     return {"lanes": out[0], "atoms_per_thread": out[1], "neigh_cap": out[2],
             "pruned_list": bool(out[3])}
-
-
-def pta_get_scheme(h) -> dict:
-    out = (ctypes.c_int32 * 4)()
-    _check(load().pta_get_scheme(h, out), "pta_get_scheme")
-    return {"scheme": {PAIRS_STENCIL: "stencil", PAIRS_LISTS: "lists"}.get(out[0], "?"),
-            "keys": out[1], "checks": out[2], "stencil_lanes": out[3]}
 
 
 def pta_relax(h, window: int, max_steps: int, tol_gpa: float):
@@ -524,9 +514,6 @@ class Ctx:
 
     def layout(self):
         return pta_get_layout(self.h)
-
-    def scheme(self):
-        return pta_get_scheme(self.h)
 
     def mean_positions(self):
         return pta_get_mean_positions(self.h, self.n)

@@ -20,7 +20,7 @@ OUT = os.path.join(PKG, "_lib")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libpta.so")
 SOURCES = ["pta_api.cu", "k_setup.cu", "k_neigh.cu", "k_pair_f32.cu", "k_pair_f64.cu",
-           "k_stencil.cu", "k_noalloc.cu", "k_peak.cu"]
+           "k_noalloc.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INC,
          "-I" + CSRC]

@@ -1,7 +1,7 @@
-// Device pieces of the mixed-precision form shared by the neighbour-list and
-// the lattice-stencil pair kernels: the FP32 pair terms of the Sutton-Chen
-// EAM (Eqs. (pe), (f_int)), the exact hi/lo velocity pair, and the per-atom
-// velocity-Verlet update of Eqs. (vv_algo_*) fused behind the force pass.
+// Device pieces of the mixed-precision pair kernels: the FP32 pair terms of
+// the Sutton-Chen EAM (Eqs. (pe), (f_int)), the exact hi/lo velocity pair,
+// and the per-atom velocity-Verlet update of Eqs. (vv_algo_*) fused behind
+// the force pass.
 //
 // Precision: pair terms in FP32 on relative coordinates; positions are an
 // exact FP32 pair x = hi + lo (hi on a 2^-12 A grid, |lo| <= 2^-13 A);
@@ -63,43 +63,43 @@ __device__ __forceinline__ float2 rsqrt2_nr(float2 r2) {
 
 // phi_m of two pairs at once (squared distances r2), for the density sum;
 // the caller adds the halves whose r2 is below rc^2, in order
-__device__ __forceinline__ float2 phi_m2_sc76(const PotDev &P, float2 r2) {
+__device__ __forceinline__ float2 phi_m2_sc76(const PotF &P, float2 r2) {
     const float2 ir = rsqrt2_nr(r2);
-    const float2 s = __fmul2_rn(f2(P.f_a), ir);
+    const float2 s = __fmul2_rn(f2(P.a), ir);
     const float2 s2 = __fmul2_rn(s, s);
     const float2 s3 = __fmul2_rn(s2, s);
     const float2 s6 = __fmul2_rn(s3, s3);
-    const float2 u = __fadd2_rn(__fmul2_rn(r2, ir), f2(-P.f_rc));
-    return __ffma2_rn(f2(P.f_Bm), u, __fadd2_rn(s6, f2(-P.f_Am)));
+    const float2 u = __fadd2_rn(__fmul2_rn(r2, ir), f2(-P.rc));
+    return __ffma2_rn(f2(P.Bm), u, __fadd2_rn(s6, f2(-P.Am)));
 }
 
 // phi_m of one pair (r2 < rc^2)
 template <bool SC76>
-__device__ __forceinline__ float phi_m1(const PotDev &P, float r2) {
+__device__ __forceinline__ float phi_m1(const PotF &P, float r2) {
     const float ir = rsqrt_nr(r2);
-    const float s = P.f_a * ir;
-    return PowF<SC76>::pm(s, P.m) - P.f_Am + P.f_Bm * (r2 * ir - P.f_rc);
+    const float s = P.a * ir;
+    return PowF<SC76>::pm(s, P.m) - P.Am + P.Bm * (r2 * ir - P.rc);
 }
 
 // one pair's contribution to the force on the unit's atom and to its pair
 // energy sum: displacement (ex, ey, ez) = r_j - r_i, r2 = |r_j - r_i|^2 < rc^2,
 // fpi + fpj = B'(rho_i) + B'(rho_j)
 template <bool SC76>
-__device__ __forceinline__ void force_pair(const PotDev &P, float ex, float ey, float ez, float r2,
+__device__ __forceinline__ void force_pair(const PotF &P, float ex, float ey, float ez, float r2,
                                            float fpij, float &fx, float &fy, float &fz,
                                            float &en) {
     const float ir = rsqrt_nr(r2);
     const float r = r2 * ir;
-    const float s = P.f_a * ir;
+    const float s = P.a * ir;
     float sn, sm;
     PowF<SC76>::pw(s, P.n, P.m, sn, sm);
-    const float dphn = -(float)P.n * sn * ir + P.f_Bn;
-    const float dphm = -(float)P.m * sm * ir + P.f_Bm;
-    const float gg = (P.f_eps * dphn + fpij * dphm) * ir;
+    const float dphn = -(float)P.n * sn * ir + P.Bn;
+    const float dphm = -(float)P.m * sm * ir + P.Bm;
+    const float gg = (P.eps * dphn + fpij * dphm) * ir;
     fx += gg * ex;
     fy += gg * ey;
     fz += gg * ez;
-    en += sn - P.f_An + P.f_Bn * (r - P.f_rc);
+    en += sn - P.An + P.Bn * (r - P.rc);
 }
 
 // (h, l) += d exactly up to the final renormalisation: Knuth's two-sum of h
@@ -122,7 +122,7 @@ __device__ __forceinline__ void hl_add(float &h, float &l, float d) {
 // next step; the new position (hi + lo, whole grid quanta moved from lo to
 // hi), its neighbour record (position relative to the reference point C,
 // written at record index rec), and the displacements since the last list
-// build or stencil check (and, with `pruned`, since the last pruning).  Grip
+// build (and, with `pruned`, since the last pruning).  Grip
 // atoms keep v = 0.  MODE_EVAL stores F and the energy instead.
 __device__ __forceinline__ void atom_update_mixed(const SpecDev &S, SpecCtl *ctl, int par, int a,
                                                   long long rec, float3 C, bool pruned, float fpa,

@@ -21,7 +21,6 @@ namespace pta {
 
 __device__ __forceinline__ bool build_active(const SpecDev &S, int force) {
     const SpecCtl *c = S.ctl;
-    if (c->scheme != SCHEME_LIST) return false;
     if (force) return true;
     if (c->phase == PH_IDLE) return false;
     return c->rebuild != 0 || c->list_L != S.L;
@@ -393,18 +392,15 @@ __global__ void k_reset_maxnn(const SpecDev *__restrict__ specs, int force) {
     if (threadIdx.x == 0) S.ctl->max_nn = 0;
 }
 
-// one block: does any specimen of the table need a list build or a stencil
-// check, or only a pruning of its inner list, before its next pair pass?
-// Sets the condition of the graph node that holds that work (LIST_BUILD,
-// LIST_PRUNE, LIST_NONE).
+// one block: does any specimen of the table need a list build, or only a
+// pruning of its inner list, before its next pair pass?  Sets the condition
+// of the graph node that holds that work (LIST_BUILD, LIST_PRUNE, LIST_NONE).
 __global__ void k_decide_rebuild(const SpecDev *__restrict__ specs, int nspec,
                                  cudaGraphConditionalHandle handle) {
     int build = 0, prune = 0;
     for (int s = threadIdx.x; s < nspec; s += blockDim.x) {
-        const SpecCtl *c = specs[s].ctl;
-        build |= build_active(specs[s], 0) ||
-                 (c->scheme == SCHEME_STENCIL && c->phase != PH_IDLE && c->rebuild != 0);
-        prune |= c->scheme == SCHEME_LIST && prune_active(specs[s], 0);
+        build |= build_active(specs[s], 0);
+        prune |= prune_active(specs[s], 0);
     }
     build = __syncthreads_or(build);
     prune = __syncthreads_or(prune);

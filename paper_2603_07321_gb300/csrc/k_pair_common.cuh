@@ -157,10 +157,7 @@ __device__ inline void step_tail(const SpecDev &S, int lb, int nblk, double ke_w
         } else if (phase == PH_REFRESH) {
             c->phase = PH_RUN;
         }
-        // the skin test: the list skin, or the stencil's own skin
-        const double hs2 = c->scheme == SCHEME_STENCIL ? (double)S.st_half_skin2
-                                                       : (double)S.half_skin2;
-        c->rebuild = (md2 > hs2) ? 1 : 0;
+        c->rebuild = (md2 > (double)S.half_skin2) ? 1 : 0;
         if (S.prune_on && mp2 > (double)S.half_prune2) c->prune = 1;
         c->parity ^= 1;
     }

@@ -18,14 +18,9 @@
 // velocity-Verlet update fused behind it (atom_update_mixed).  Grip atoms
 // keep v = 0 and F = 0 in the update; their internal force still enters the
 // reaction R = -sum_{right grip} F . e of Eq. (state_variables).
-//
-// Every kernel here serves specimens on the list scheme; a specimen on the
-// lattice stencil (k_stencil.cu) returns at once.
 #include "k_mixed.cuh"
 
 namespace pta {
-
-__device__ __forceinline__ bool on_lists(const SpecCtl *c) { return c->scheme == SCHEME_LIST; }
 
 // The entry loop is unrolled by two (by four in the density pass); the next
 // two (four) entries are read before the current ones are evaluated.  Those
@@ -72,12 +67,12 @@ __device__ __forceinline__ void entry_disp2(unsigned ea, unsigned eb, float4 xa,
 
 // density terms of two entries (b only when vb), added in entry order
 template <bool SC76>
-__device__ __forceinline__ void rho_add2(const PotDev &P, float2 dx, float2 dy, float2 dz, bool vb,
+__device__ __forceinline__ void rho_add2(const PotF &P, float2 dx, float2 dy, float2 dz, bool vb,
                                          float &rho) {
     float2 r2 = __fmul2_rn(dx, dx);
     r2 = __ffma2_rn(dy, dy, r2);
     r2 = __ffma2_rn(dz, dz, r2);
-    const float rc2 = P.f_rc2;
+    const float rc2 = P.rc2;
     if (SC76) {
         const float2 phi = phi_m2_sc76(P, r2);
         if (r2.x < rc2) rho += phi.x;
@@ -90,10 +85,11 @@ __device__ __forceinline__ void rho_add2(const PotDev &P, float2 dx, float2 dy, 
 
 template <int L, bool SC76>
 __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restrict__ specs,
-                                                        const int *__restrict__ b2s, int force) {
+                                                        const int *__restrict__ b2s, int force,
+                                                        const PotF P) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     const SpecCtl *ctl = S.ctl;
-    if (!on_lists(ctl) || (!force && ctl->phase == PH_IDLE)) return;
+    if (!force && ctl->phase == PH_IDLE) return;
     const int par = ctl->parity;
     constexpr int UPB = TPB / L;
     const int u = (blockIdx.x - S.blk_pair0) * UPB + threadIdx.x / L;
@@ -116,10 +112,10 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
                 const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
                 float2 dx, dy, dz;
                 entry_disp2(e0, e1, x0, x1, ra, h, h8, h64, dx, dy, dz);
-                rho_add2<SC76>(S.pot, dx, dy, dz, q + 1 < cl, rho);
+                rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
                 if (q + 2 < cl) {
                     entry_disp2(e2, e3, x2, x3, ra, h, h8, h64, dx, dy, dz);
-                    rho_add2<SC76>(S.pot, dx, dy, dz, q + 3 < cl, rho);
+                    rho_add2<SC76>(P, dx, dy, dz, q + 3 < cl, rho);
                 }
                 e0 = n0; e1 = n1; e2 = n2; e3 = n3;
             }
@@ -131,7 +127,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
                 const float4 xb = __ldg(rel + nl_j(eb));
                 float2 dx, dy, dz;
                 entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
-                rho_add2<SC76>(S.pot, dx, dy, dz, q + 1 < cl, rho);
+                rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
                 ea = na;
                 eb = nb;
             }
@@ -139,18 +135,19 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
     }
     rho = lane_sum<L>(rho);
     if (valid && l == 0) {
-        const float fp = rho > 0.f ? -0.5f * S.pot.f_ec * rsqrtf(rho) : 0.f;
+        const float fp = rho > 0.f ? -0.5f * P.ec * rsqrtf(rho) : 0.f;
         ((float4 *)S.posfp)[u] = make_float4(ra.x, ra.y, ra.z, fp);
     }
 }
 
 template <int L, bool SC76>
 __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict__ specs,
-                                                      const int *__restrict__ b2s, int mode) {
+                                                      const int *__restrict__ b2s, int mode,
+                                                      const PotF P) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     SpecCtl *ctl = S.ctl;
     const int phase = ctl->phase;
-    if (!on_lists(ctl) || (mode == MODE_STEP && phase == PH_IDLE)) return;
+    if (mode == MODE_STEP && phase == PH_IDLE) return;
     const int par = ctl->parity;
     const long long done = ctl->done, nsteps = ctl->nsteps;
     constexpr int UPB = TPB / L;
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
     const bool valid = u < S.n;
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
     const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
-    const float rc2 = S.pot.f_rc2;
+    const float rc2 = P.rc2;
     float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f;
     float4 ra = make_float4(0, 0, 0, 0);
     if (valid) {
@@ -177,10 +174,10 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
             float2 dx, dy, dz;
             entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
             const float r2a = dx.x * dx.x + dy.x * dy.x + dz.x * dz.x;
-            if (r2a < rc2) force_pair<SC76>(S.pot, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, en);
+            if (r2a < rc2) force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, en);
             const float r2b = dx.y * dx.y + dy.y * dy.y + dz.y * dz.y;
             if (q + 1 < cl && r2b < rc2)
-                force_pair<SC76>(S.pot, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, en);
+                force_pair<SC76>(P, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, en);
             ea = na;
             eb = nb;
         }
@@ -211,7 +208,7 @@ template <int L>
 __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict__ specs,
                                                       const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
-    if (S.prec == PTA_PREC_FP64 || !on_lists(S.ctl) || !prune_active(S, force)) return;
+    if (S.prec == PTA_PREC_FP64 || !prune_active(S, force)) return;
     const SpecCtl *ctl = S.ctl;
     const int par = ctl->parity;
     constexpr int UPB = TPB / L;
@@ -244,7 +241,7 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
 // of the pruning kernel reads the same flag)
 __global__ void k_prune_done(const SpecDev *__restrict__ specs, int force) {
     const SpecDev &S = specs[blockIdx.x];
-    if (!on_lists(S.ctl) || !prune_active(S, force)) return;
+    if (!prune_active(S, force)) return;
     if (threadIdx.x == 0) {
         S.ctl->prune = 0;
         S.ctl->prunes += 1;
@@ -254,7 +251,7 @@ __global__ void k_prune_done(const SpecDev *__restrict__ specs, int force) {
 void launch_prune(const Tab &t, int force, cudaStream_t st) {
     for (int i = 0; i < t.ngroups; ++i) {
         const Group &g = t.grp[i];
-        if (g.nblk <= 0 || g.prec == PTA_PREC_FP64 || g.scheme != SCHEME_LIST) continue;
+        if (g.nblk <= 0 || g.prec == PTA_PREC_FP64) continue;
         switch (g.L) {
             case 1: k_prune_f32<1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
             case 2: k_prune_f32<2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
@@ -267,29 +264,25 @@ void launch_prune(const Tab &t, int force, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// dispatch by (scheme, precision, lanes, potential variant)
+// dispatch by (precision, lanes, potential variant)
 // ---------------------------------------------------------------------------
 void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st);
 void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st);
-void launch_density_stencil(const Tab &t, const Group &g, int force, cudaStream_t st);
-void launch_force_stencil(const Tab &t, const Group &g, int mode, cudaStream_t st);
 
 #define PTA_L_SWITCH(KER, SC)                                                            \
     switch (g.L) {                                                                       \
-        case 1: KER<1, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg); break;          \
-        case 2: KER<2, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg); break;          \
-        case 4: KER<4, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg); break;          \
-        case 8: KER<8, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg); break;          \
-        default: KER<16, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg); break;        \
+        case 1: KER<1, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg, g.pf); break;    \
+        case 2: KER<2, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg, g.pf); break;    \
+        case 4: KER<4, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg, g.pf); break;    \
+        case 8: KER<8, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg, g.pf); break;    \
+        default: KER<16, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, arg, g.pf); break;  \
     }
 
 void launch_density(const Tab &t, int arg, cudaStream_t st) {
     for (int i = 0; i < t.ngroups; ++i) {
         const Group &g = t.grp[i];
         if (g.nblk <= 0) continue;
-        if (g.scheme == SCHEME_STENCIL)
-            launch_density_stencil(t, g, arg, st);
-        else if (g.prec == PTA_PREC_FP64)
+        if (g.prec == PTA_PREC_FP64)
             launch_density_f64(t, g, arg, st);
         else if (g.sc76)
             PTA_L_SWITCH(k_density_f32, true)
@@ -302,9 +295,7 @@ void launch_force(const Tab &t, int arg, cudaStream_t st) {
     for (int i = 0; i < t.ngroups; ++i) {
         const Group &g = t.grp[i];
         if (g.nblk <= 0) continue;
-        if (g.scheme == SCHEME_STENCIL)
-            launch_force_stencil(t, g, arg, st);
-        else if (g.prec == PTA_PREC_FP64)
+        if (g.prec == PTA_PREC_FP64)
             launch_force_f64(t, g, arg, st);
         else if (g.sc76)
             PTA_L_SWITCH(k_force_f32, true)

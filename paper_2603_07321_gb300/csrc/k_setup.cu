@@ -262,8 +262,7 @@ __global__ void k_export(const SpecDev *__restrict__ sp) {
 // checkpoints: the raw working state (current position buffer, velocities,
 // grip flags) gathered into creation order through the permutation scratch,
 // or scattered back to the context's current slot order, so that a
-// checkpoint does not depend on how atoms are ordered in memory (by cell
-// for the lists, by lattice row for the stencil)
+// checkpoint does not depend on how the last list build ordered the atoms
 __global__ void k_ckpt_move(const SpecDev *__restrict__ sp, int gather) {
     const SpecDev &S = *sp;
     const int a = blockIdx.x * TPB + threadIdx.x;

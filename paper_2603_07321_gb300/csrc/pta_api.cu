@@ -266,10 +266,6 @@ struct Sizes {
     double h, org[3];
     size_t list_words;
     long long series_cap;
-    // lattice stencil
-    int stencil, Lst, nblk_st, NKp, NYp, NZp;
-    long long nslot;
-    double st_skin;
 };
 
 // threads per atom chosen from the specimen alone (so that a specimen runs
@@ -332,30 +328,15 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
     if (ncell > (1LL << 30)) return PTA_EINVAL;
     z->ncell = (int)ncell;
     z->nblk_cell = (z->ncell + CELL_WARPS * CELLS_PER_WARP - 1) / (CELL_WARPS * CELLS_PER_WARP);
-    // words of the list: the layout of L lanes, or of one lane (the stencil's
-    // lists for pta_get_neighbours), whichever is larger
     const long long W = 32 / z->L;
-    z->list_words = std::max<size_t>((size_t)((z->n + W - 1) / W) * W * z->cap,
-                             (size_t)((z->n + 31) / 32) * 32 * z->cap);
+    z->list_words = (size_t)((z->n + W - 1) / W) * W * z->cap;
     z->series_cap = std::max<long long>(par.burst_steps, 1);
-    // lattice stencil: mixed precision unless lists are asked for; its own
-    // skin (default 1 A) within the cell edge
-    z->stencil = (par.precision == PTA_PREC_MIXED && par.pair_scheme != PTA_PAIRS_LISTS) ? 1 : 0;
-    z->st_skin = par.stencil_skin > 0.0 ? std::min(par.stencil_skin, par.skin)
-                                        : std::min(1.0, par.skin);
-    z->Lst = std::min(par.lanes ? par.lanes : auto_lanes(z->n, par.precision), 8);
-    z->NKp = s.n_cells[0] + 2 * ST_PK;
-    z->NYp = 2 * s.n_cells[1] + 2 * ST_R;
-    z->NZp = 2 * s.n_cells[2] + 2 * ST_R;
-    z->nslot = z->stencil ? (long long)z->NKp * z->NYp * z->NZp : 0;
-    z->nblk_st = z->stencil ? (int)((z->n * z->Lst + TPB - 1) / TPB) : 0;
     return PTA_OK;
 }
 
 static size_t footprint(const Sizes &z, int prec) {
     const size_t n = (size_t)z.n;
     const size_t p = (prec == PTA_PREC_FP64) ? 32 : 16;
-    const size_t nrec = std::max<size_t>(n, (size_t)z.nslot);  // records: padded for the stencil
     size_t b = 0;
     auto add = [&](size_t x) { b += round_up(x > 0 ? x : 1, 256); };
     add(p * n);
@@ -363,11 +344,11 @@ static size_t footprint(const Sizes &z, int prec) {
     if (prec != PTA_PREC_FP64) {
         add(16 * n);
         add(16 * n);                 // lo[2]
-        add(16 * nrec);
-        add(16 * nrec);              // rel[2]
+        add(16 * n);
+        add(16 * n);                 // rel[2]
         add(n);                      // hsub
     }
-    add(p * nrec);                   // posfp
+    add(p * n);                      // posfp
     add(32 * n);                     // vel (double4 or hi/lo FP32)
     add(n);                          // flags
     add(16 * n);                     // ref
@@ -385,13 +366,7 @@ static size_t footprint(const Sizes &z, int prec) {
         add(16 * n);                 // pref
     }
     add(4 * n);                      // nn
-    if (z.stencil) {
-        add(4 * n);                    // st_sites
-        add(4 * (size_t)z.nslot);      // st_inv
-        add(16 * 2 * (size_t)ST_TAB);  // st_tab
-        add(4 * (size_t)ST_WORDS);     // st_bits
-    }
-    add(64 * (size_t)std::max(std::max(z.nblk_pair, z.nblk_atom), z.nblk_st));  // part
+    add(64 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
     if (z.mean_pos) add(32 * n);     // rsum
@@ -421,10 +396,6 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
     if (par->neigh_cap < 0 || par->neigh_cap > 4096) return PTA_EINVAL;
     if (par->cell_tiles < -1 || par->cell_tiles > 1) return PTA_EINVAL;
     if (par->cell_tiles == 1) return PTA_EUNSUPPORTED;
-    if (par->pair_scheme < PTA_PAIRS_AUTO || par->pair_scheme > PTA_PAIRS_LISTS) return PTA_EINVAL;
-    if (par->pair_scheme == PTA_PAIRS_STENCIL && par->precision == PTA_PREC_FP64)
-        return PTA_EUNSUPPORTED;
-    if (!std::isfinite(par->stencil_skin) || par->stencil_skin < 0.0) return PTA_EINVAL;
     if (!std::isfinite(par->prune_margin)) return PTA_EINVAL;
     if (par->conv_lag < 0) return PTA_EINVAL;
     if (par->mean_positions != 0 && par->mean_positions != 1) return PTA_EINVAL;
@@ -521,12 +492,7 @@ static int capture_iters(Runner *r, int iters, cudaGraphExec_t *out, bool timed 
                 rc = PTA_ECUDA;
                 break;
             }
-            if (b == (int)LIST_BUILD) {
-                // stencil checks first: a specimen that leaves the stencil
-                // gets its list from the build right behind them
-                launch_stencil_check(r->tab, 0, 0.0, r->cap2);
-                launch_rebuild(r->tab, 0, r->cap2);
-            }
+            if (b == (int)LIST_BUILD) launch_rebuild(r->tab, 0, r->cap2);
             launch_prune(r->tab, 0, r->cap2);
             cudaGraph_t bout = nullptr;
             if (cudaStreamEndCapture(r->cap2, &bout) != cudaSuccess) rc = PTA_ECUDA;
@@ -559,7 +525,6 @@ static int capture_iters_flat(Runner *r, int iters, cudaGraphExec_t *out, bool t
     CK(cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < iters; ++i) {
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 0], r->cap, cudaEventRecordExternal);
-        launch_stencil_check(r->tab, 0, 0.0, r->cap);
         launch_rebuild(r->tab, 0, r->cap);
         launch_prune(r->tab, 0, r->cap);
         if (timed) cudaEventRecordWithFlags(r->ev[4 * i + 1], r->cap, cudaEventRecordExternal);
@@ -588,18 +553,18 @@ static int runner_upload(Runner *r) {
     r->hspecs.resize(k);
     int blk_atom = 0, blk_cell = 0;
     std::vector<int> b2s_atom, b2s_cell;
-    // launch groups by (scheme, precision, lanes, potential variant); a
-    // stencil specimen has blocks in a stencil group and in a list group
-    // (the list kernels serve it once it leaves the stencil)
+    // launch groups by (precision, lanes, potential); the potential's FP32
+    // constants are kernel parameters of the group's launches
     struct Key {
-        int prec, L, sc76, scheme;
+        int prec, L, sc76;
+        PotF pf;
     };
     std::vector<Key> keys;
     std::vector<std::vector<int>> gb2s;
     auto group_of = [&](const Key &kk) -> int {
         for (size_t q = 0; q < keys.size(); ++q)
             if (keys[q].prec == kk.prec && keys[q].L == kk.L && keys[q].sc76 == kk.sc76 &&
-                keys[q].scheme == kk.scheme)
+                std::memcmp(&keys[q].pf, &kk.pf, sizeof(PotF)) == 0)
                 return (int)q;
         if (keys.size() >= 8) return -1;
         keys.push_back(kk);
@@ -615,16 +580,23 @@ static int runner_upload(Runner *r) {
         s.blk_cell0 = blk_cell;
         blk_cell += s.nblk_cell;
         for (int b = 0; b < s.nblk_cell; ++b) b2s_cell.push_back(i);
-        int g = group_of({s.prec, s.L, s.pot.sc76, SCHEME_LIST});
+        PotF pf;
+        std::memset(&pf, 0, sizeof(pf));
+        pf.a = s.pot.f_a;
+        pf.rc = s.pot.f_rc;
+        pf.rc2 = s.pot.f_rc2;
+        pf.Am = s.pot.f_Am;
+        pf.Bm = s.pot.f_Bm;
+        pf.An = s.pot.f_An;
+        pf.Bn = s.pot.f_Bn;
+        pf.eps = s.pot.f_eps;
+        pf.ec = s.pot.f_ec;
+        pf.n = s.pot.n;
+        pf.m = s.pot.m;
+        const int g = group_of({s.prec, s.L, s.pot.sc76, pf});
         if (g < 0) return PTA_EUNSUPPORTED;
         s.blk_pair0 = (int)gb2s[g].size();
         for (int b = 0; b < s.nblk_pair; ++b) gb2s[g].push_back(i);
-        if (s.stencil) {
-            g = group_of({s.prec, s.Lst, s.pot.sc76, SCHEME_STENCIL});
-            if (g < 0) return PTA_EUNSUPPORTED;
-            s.blk_st0 = (int)gb2s[g].size();
-            for (int b = 0; b < s.nblk_st; ++b) gb2s[g].push_back(i);
-        }
         r->hspecs[i] = s;
     }
     // one device block for all tables
@@ -676,7 +648,7 @@ static int runner_upload(Runner *r) {
         t.grp[q].prec = keys[q].prec;
         t.grp[q].L = keys[q].L;
         t.grp[q].sc76 = keys[q].sc76;
-        t.grp[q].scheme = keys[q].scheme;
+        t.grp[q].pf = keys[q].pf;
         t.grp[q].b2s = tabs + off;
         t.grp[q].nblk = (int)gb2s[q].size();
         off += gb2s[q].size();
@@ -982,8 +954,6 @@ int pta_default_params(pta_params *p) {
     p->neigh_cap = 0;
     p->lanes = 0;
     p->cell_tiles = 0;
-    p->pair_scheme = PTA_PAIRS_AUTO;
-    p->stencil_skin = 0.0;
     p->conv_lag = 0;
     p->mean_positions = 0;
     p->conv_tol[0] = p->conv_tol[1] = p->conv_tol[2] = 0.05;
@@ -1017,7 +987,6 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     const size_t n = (size_t)z.n;
     const bool f64 = c->par.precision == PTA_PREC_FP64;
     const size_t p = f64 ? 32 : 16;
-    const size_t nrec = std::max<size_t>(n, (size_t)z.nslot);
     void *q;
 #define AL(field, bytes, type) \
     CKR(dev_alloc(c, (bytes), &q)); \
@@ -1027,11 +996,11 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     if (!f64) {
         AL(lo[0], 16 * n, float4 *);
         AL(lo[1], 16 * n, float4 *);
-        AL(rel[0], 16 * nrec, float4 *);
-        AL(rel[1], 16 * nrec, float4 *);
+        AL(rel[0], 16 * n, float4 *);
+        AL(rel[1], 16 * n, float4 *);
         AL(hsub, n, uint8_t *);
     }
-    AL(posfp, p * nrec, void *);
+    AL(posfp, p * n, void *);
     AL(vel, 32 * n, void *);
     AL(flags, n, uint8_t *);
     AL(ref, 16 * n, float4 *);
@@ -1049,13 +1018,7 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
         AL(pref, 16 * n, float4 *);
     }
     AL(nn, 4 * n, int *);
-    if (z.stencil) {
-        AL(st_sites, 4 * n, int *);
-        AL(st_inv, 4 * (size_t)z.nslot, int *);
-        AL(st_tab, 16 * 2 * (size_t)ST_TAB, int4 *);
-        AL(st_bits, 4 * (size_t)ST_WORDS, unsigned *);
-    }
-    AL(part, 64 * (size_t)std::max(std::max(z.nblk_pair, z.nblk_atom), z.nblk_st), double *);
+    AL(part, 64 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
     if (z.mean_pos) {
@@ -1106,19 +1069,6 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
     s.nblk_pair = z.nblk_pair;
     s.nblk_atom = z.nblk_atom;
     s.nblk_cell = z.nblk_cell;
-    s.stencil = z.stencil;
-    s.Lst = z.Lst;
-    s.nblk_st = z.nblk_st;
-    s.NKp = z.NKp;
-    s.NYp = z.NYp;
-    s.NZp = z.NZp;
-    s.nslot = z.nslot;
-    {
-        const double rs = c->pot.rc + z.st_skin;
-        s.st_rl2 = rs * rs;
-        s.f_st_rl2 = (float)(s.st_rl2 * (1.0 + 1e-5));
-        s.st_half_skin2 = (float)(0.25 * z.st_skin * z.st_skin);
-    }
     for (int d = 0; d < 3; ++d) {
         s.ncl[d] = c->spec.n_cells[d];
         s.org[d] = z.org[d];
@@ -1176,38 +1126,10 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
                             c->stream) != cudaSuccess)
             rc = PTA_ECUDA;
     }
-    // stencil: the brick order of the atoms (site of every slot, packed
-    // k | Y << 10 | Z << 20) and its inverse over the padded record slots
-    std::vector<int> st_sites, st_inv;
-    if (rc == PTA_OK && s.stencil) {
-        const int nx = c->spec.n_cells[0], ny2 = 2 * c->spec.n_cells[1],
-                  nz2 = 2 * c->spec.n_cells[2];
-        st_sites.reserve((size_t)s.n);
-        st_inv.assign((size_t)s.nslot, -1);
-        for (int bz = 0; bz < nz2; bz += ST_BZ)
-            for (int by = 0; by < ny2; by += ST_BY)
-                for (int bk = 0; bk < nx; bk += ST_BK)
-                    for (int Z = bz; Z < std::min(bz + ST_BZ, nz2); ++Z)
-                        for (int Y = by; Y < std::min(by + ST_BY, ny2); ++Y)
-                            for (int k = bk; k < std::min(bk + ST_BK, nx); ++k) {
-                                const long long ps =
-                                    ((long long)(Z + ST_R) * s.NYp + (Y + ST_R)) * s.NKp + k + ST_PK;
-                                st_inv[(size_t)ps] = (int)st_sites.size();
-                                st_sites.push_back(k | (Y << 10) | (Z << 20));
-                            }
-        if ((long long)st_sites.size() != s.n ||
-            cudaMemcpyAsync(s.st_sites, st_sites.data(), 4 * st_sites.size(),
-                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-            cudaMemcpyAsync(s.st_inv, st_inv.data(), 4 * st_inv.size(), cudaMemcpyHostToDevice,
-                            c->stream) != cudaSuccess)
-            rc = PTA_ECUDA;
-    }
     if (rc == PTA_OK) {
         const double kT = kb_ev() * T0;
         const double sigma = std::sqrt(kT / (s.mass * mv2_to_ev()));
         launch_create(c->hd, c->d_self, sigma, kT, seed, c->stream);
-        // the stencil keeps atoms in lattice row order from the start
-        if (s.stencil) launch_stencil_order(c->hd, c->d_self, c->stream);
         launch_import(c->hd, c->d_self, c->stream);
         rc = launch_check();
     }
@@ -1256,19 +1178,6 @@ int pta_get_layout(const pta_ctx *c, int32_t out[4]) {
     out[1] = 1;
     out[2] = c->hd.cap_use;
     out[3] = c->hd.prune_on;
-    return PTA_OK;
-}
-
-int pta_get_scheme(pta_ctx *c, int32_t out[4]) {
-    if (!c || !out) return PTA_EINVAL;
-    if (c->broken) return PTA_ECUDA;
-    SpecCtl ctl;
-    CK(cudaMemcpyAsync(&ctl, c->hd.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    out[0] = ctl.scheme == SCHEME_STENCIL ? PTA_PAIRS_STENCIL : PTA_PAIRS_LISTS;
-    out[1] = ctl.scheme == SCHEME_STENCIL ? ctl.nkey : 0;
-    out[2] = ctl.st_checks;
-    out[3] = c->hd.stencil ? c->hd.Lst : 0;
     return PTA_OK;
 }
 
@@ -1452,7 +1361,6 @@ int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     if (!c || n != c->hd.n) return PTA_EINVAL;
     Runner *r;
     CKR(ctx_solo(c, &r));
-    launch_stencil_check(r->tab, 1, 0.0, c->stream);
     launch_rebuild(r->tab, 1, c->stream);
     launch_prune(r->tab, 1, c->stream);
     launch_density(r->tab, 1, c->stream);
@@ -1485,24 +1393,9 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     CKR(ctx_solo(c, &r));
     const SpecDev &s = c->hd;
     SpecCtl ctl;
-    bool st = false;
-    if (s.stencil) {
-        // the stencil checked at the list radius, then its pairs within that
-        // radius (a check that leaves the stencil falls back to the lists)
-        launch_stencil_check(r->tab, 1, s.rl2, c->stream);
-        CKR(launch_check());
-        CK(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        st = ctl.scheme == SCHEME_STENCIL;
-    }
-    if (st) {
-        CK(cudaMemsetAsync(&s.ctl->max_nn, 0, sizeof(int), c->stream));
-        launch_stencil_list(c->hd, c->d_self, c->stream);
-    } else {
-        launch_rebuild(r->tab, 1, c->stream);
-    }
+    launch_rebuild(r->tab, 1, c->stream);
     CKR(launch_check());
-    const int L = st ? 1 : s.L;
+    const int L = s.L;
     std::vector<int> nn((size_t)n), raw;
     CK(cudaMemcpyAsync(nn.data(), s.nn, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream));
@@ -1533,7 +1426,7 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
 
 // checkpoint layout: header, PtaDev, then the raw working arrays of the
 // current position buffer, the velocities and the grip flags, in creation
-// order (independent of the slot order the pair scheme keeps)
+// order (independent of the order the last list build left the atoms in)
 struct CkptHeader {
     char magic[8];
     int32_t version, prec;

@@ -28,32 +28,6 @@ constexpr double MIXED_RANGE = 511.0;
 
 enum Phase : int { PH_IDLE = 0, PH_REFRESH = 1, PH_RUN = 2 };
 enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4 };
-// how a specimen's pair passes find neighbours: Verlet lists, or the lattice
-// stencil (mixed precision; a specimen leaves the stencil for lists on the
-// device once its neighbour pairs no longer fit the stencil's range)
-enum Scheme : int { SCHEME_LIST = 0, SCHEME_STENCIL = 1 };
-
-// Atoms of a stencil specimen are kept in brick order: bricks of ST_BK sites
-// along a row x ST_BY rows along y x ST_BZ rows along z, bricks in (z, y, x)
-// order, sites within a brick in (z, y, x) order, so that a thread block's
-// atoms form a compact block of the crystal (its neighbours' records stay in
-// L1) while a warp still reads runs of ST_BK consecutive records.
-constexpr int ST_BK = 8, ST_BY = 4, ST_BZ = 4;
-
-// Lattice stencil (k_stencil.cu): lattice vectors in units of a0 / 2 with
-// every component in [-ST_R, ST_R]; at most ST_KEYS of them; the padded
-// record arrays extend ST_PK sites along each row and ST_R rows along y and z
-// beyond the lattice, so that every stencil neighbour of a lattice site has
-// a slot
-constexpr int ST_R = 10;
-constexpr int ST_SIDE = 2 * ST_R + 1;
-constexpr int ST_BITS = ST_SIDE * ST_SIDE * ST_SIDE;
-constexpr int ST_WORDS = (ST_BITS + 31) / 32;
-constexpr int ST_KEYS = 1024;
-constexpr int ST_TAB = ST_KEYS + 64;  // entries per parity table (spare far entries at the end)
-constexpr int ST_PK = (ST_R + 1) / 2;
-constexpr float ST_FAR = 1.0e4f;      // coordinate of the records of empty slots (A)
-
 // mixed precision: velocity as an exact FP32 pair v = h + l
 struct __align__(32) VelHL {
     float4 h, l;
@@ -69,6 +43,14 @@ struct PotDev {
     int n, m;
     float f_eps, f_a, f_rc, f_rc2, f_An, f_Bn, f_Am, f_Bm, f_ec, f_ec2h;
     int sc76;  // 1 when (n, m) == (7, 6): the fast specialised kernels apply
+};
+
+// FP32 constants of the pair terms, passed by value to the mixed-precision
+// pair kernels: read from the kernel's constant bank at every use, they cost
+// no load and no register inside the pair loops
+struct PotF {
+    float a, rc, rc2, Am, Bm, An, Bn, eps, ec;
+    int n, m;
 };
 
 // slow-variable record of the coarse-step logic (FP64)
@@ -91,12 +73,6 @@ struct SpecCtl {
     int max_nn;                // largest neighbour count at the last build
     int prune;                 // 1: prune the inner list before the next pair pass
     int prunes;                // prunings in the current burst
-    int scheme;                // Scheme of the pair passes (stencil specimens may fall back)
-    int nkey;                  // stencil: keys in the current table (a multiple of 4)
-    int st_err;                // stencil: the last check found pairs beyond its range or cap
-    int st_checks;             // stencil: checks since creation
-    int st_box[6];             // stencil: per-axis min and max of the positions (ordered ints)
-    float st_q[3], st_o[3];    // stencil: reference lattice, site = o + (X q_x, Y q_y, Z q_z)
     double sum[3];             // running sums of K, U, T over the burst (in step order)
     double sum_chk[3];         // adaptive length: running sums at the last check
     double conv_val[3];        // adaptive length: running average at convergence
@@ -113,20 +89,10 @@ struct SpecDev {
     // sizes
     int n, L, prec, axis, cap;   // cap: list stride per unit (usable entries: cap_use)
     int cap_use;
-    int blk_pair0, nblk_pair;  // list pair kernels: TPB/L atoms per block
-    int blk_st0, nblk_st, Lst; // stencil pair kernels: TPB/Lst atoms per block, Lst lanes each
+    int blk_pair0, nblk_pair;  // pair kernels: TPB/L atoms per block
     int blk_atom0, nblk_atom;  // one thread per atom
     int blk_cell0, nblk_cell;  // cell sort: CELLS_PER_WARP cells per warp
     int spec_index;            // index of this specimen in the launch table
-    // stencil geometry: rows of ncl[0] sites along x for every (Y, Z) in
-    // [0, 2 ncl[1]) x [0, 2 ncl[2]) (half lattice units); padded slot of
-    // site (k, Y, Z) = ((Z + ST_R) NYp + Y + ST_R) NKp + k + ST_PK
-    int stencil;               // 1: the specimen may use the stencil
-    int NKp, NYp, NZp;
-    long long nslot;           // NKp NYp NZp
-    double st_rl2;             // squared radius the stencil must cover (rc + stencil skin)^2
-    float f_st_rl2;            // its FP32 value widened by 1e-5 (the check's test)
-    float st_half_skin2;       // (stencil skin / 2)^2: a check is due beyond this displacement
     // lattice (creation only)
     int ncl[3];
     double a0, grip_width;
@@ -163,11 +129,6 @@ struct SpecDev {
     float4 *ref;    // positions at the last list build (skin test)
     int *atom_cell, *cell_cnt, *cell_start, *cell_tmp, *cell_atoms;
     int *orig;        // original index (creation order) of the atom stored at each slot
-    int *st_sites;    // stencil: site of every atom slot, k | Y << 10 | Z << 20
-    int *st_inv;      // stencil: atom slot of every padded record slot (-1: none)
-    int4 *st_tab;     // stencil: two tables of ST_TAB entries (even, odd rows):
-                      // {slot offset, c_x, c_y, c_z (float bits)} per key
-    unsigned *st_bits;  // stencil: ST_WORDS words, the keys seen by the check
     void *perm_tmp;   // scratch of the permutation that sorts atoms by cell
     int *nlist, *nn;
     int *plist, *pnn;   // inner list (same layout as nlist), entries per unit and lane
@@ -185,7 +146,8 @@ struct SpecDev {
 };
 
 struct Group {
-    int prec, L, sc76, scheme;
+    int prec, L, sc76;
+    PotF pf;  // the group's potential (specimens of one group share it)
     const int *b2s;
     int nblk;
 };
@@ -406,13 +368,6 @@ void launch_any_running(const Tab &t, int *flag, cudaStream_t st);
 void launch_pta_update(const Tab &t, const int *ops, pta_coarse_result *out, cudaStream_t st);
 void launch_force_rebuild_flag(const Tab &t, cudaStream_t st);
 void launch_rebuild(const Tab &t, int force, cudaStream_t st);
-// stencil: check the pairs within the stencil radius (rl2_override > 0: that
-// radius instead) and rebuild the key table; set up the row order at creation
-void launch_stencil_check(const Tab &t, int force, double rl2_override, cudaStream_t st);
-void launch_stencil_order(const SpecDev &h, const SpecDev *d, cudaStream_t st);
-// stencil: write each atom's stencil neighbours within sqrt(rl2) into the
-// Verlet-list arrays (FP64 predicate), for pta_get_neighbours
-void launch_stencil_list(const SpecDev &h, const SpecDev *d, cudaStream_t st);
 void launch_prune(const Tab &t, int force, cudaStream_t st);
 void launch_decide_rebuild(const Tab &t, cudaGraphConditionalHandle h, cudaStream_t st);
 // list maintenance decided on the device: 0 build + prune, 1 prune, 2 nothing

@@ -4,7 +4,7 @@ The fastest layout depends on the specimen and on how many specimens share
 the device: a small cube alone wants several threads per atom, the same cube
 in a large batch one; a bigger Verlet skin trades longer lists for fewer
 builds.  `tune` measures instead of guessing: for every candidate
-(pair scheme, threads per atom, skin) it creates the specimen (or a batch of
+(threads per atom, skin) it creates the specimen (or a batch of
 identical-size replicas), runs a short warm burst, times a burst on the
 device, and returns the candidates ranked by atom-steps per second.  Every
 candidate computes the same physics; the choice only changes speed (and, in
@@ -21,16 +21,15 @@ import time
 
 
 def tune(n_cells, precision: int = 1, replicas: int = 1, T0: float = 300.0, seed: int = 1,
-         lanes=(1, 2, 4, 8), skins=(1.0, 2.0), schemes=(0,), steps: int = 200, warm: int = 50,
+         lanes=(1, 2, 4, 8), skins=(1.0, 2.0), steps: int = 200, warm: int = 50,
          strain: float = 1e-3):
-    """Time every (pair_scheme, lanes, skin) candidate; returns (best, table):
-    best is a dict of Ctx keyword arguments, table a list of
-    (atom-steps/s, kwargs) sorted fastest first.  Candidates the library
-    rejects (e.g. the stencil in FP64) are skipped."""
+    """Time every (lanes, skin) candidate; returns (best, table): best is a
+    dict of Ctx keyword arguments, table a list of (atom-steps/s, kwargs)
+    sorted fastest first.  Candidates the library rejects are skipped."""
     from . import Batch, Ctx, PTAError
     table = []
-    for sch, L, skin in itertools.product(schemes, lanes, skins):
-        kw = dict(precision=precision, lanes=L, skin=skin, pair_scheme=sch)
+    for L, skin in itertools.product(lanes, skins):
+        kw = dict(precision=precision, lanes=L, skin=skin)
         try:
             ctxs = [Ctx(n_cells, T0=T0, seed=seed + i, **kw) for i in range(replicas)]
         except PTAError:

@@ -152,9 +152,7 @@ def test_new_parameters_are_validated_before_touching_the_gpu(P):
     h = ctypes.c_void_p()
     bad = [dict(conv_lag=-1), dict(conv_tol=(0.05, float("nan"), 0.05)),
            dict(conv_tol=(-0.1, 0.05, 0.05)), dict(mean_positions=2), dict(cell_tiles=2),
-           dict(precision=0, cell_tiles=1), dict(cell_tiles=1), dict(atoms_per_thread=2),
-           dict(pair_scheme=3), dict(pair_scheme=-1), dict(precision=0, pair_scheme=1),
-           dict(stencil_skin=-1.0)]
+           dict(precision=0, cell_tiles=1), dict(cell_tiles=1), dict(atoms_per_thread=2)]
     for kw in bad:
         par = P.default_params(**kw)
         rc = lib.pta_create(ctypes.byref(spec), ctypes.byref(pot), 300.0, 1, ctypes.byref(par),

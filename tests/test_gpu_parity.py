@@ -30,17 +30,10 @@ def test_create_matches_oracle(P, oracle, prec, shape, axis):
     ctx.close()
 
 
-LISTS, STENCIL = 2, 1
-
-
-@pytest.mark.parametrize("prec,lanes,scheme", [(0, 1, LISTS), (0, 4, LISTS), (0, 16, LISTS),
-                                                (1, 1, LISTS), (1, 4, LISTS), (1, 16, LISTS),
-                                                (1, 1, STENCIL), (1, 4, STENCIL)])
+@pytest.mark.parametrize("prec,lanes", [(0, 1), (0, 4), (0, 16), (1, 1), (1, 4), (1, 16)])
 @pytest.mark.parametrize("shape", [(5, 4, 6), (7, 7, 7)])
-def test_neighbour_sets_bit_exact(P, oracle, prec, lanes, scheme, shape):
-    # with the stencil, the lists are the stencil's pairs within the list
-    # radius: equal to the brute-force pairs only if the stencil covers them all
-    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=prec, lanes=lanes, pair_scheme=scheme)
+def test_neighbour_sets_bit_exact(P, oracle, prec, lanes, shape):
+    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=prec, lanes=lanes)
     pos = on_grid(PI.jittered_fcc(shape, 0.35, seed=sum(shape) + lanes))
     ctx.set_state(pos, np.zeros_like(pos))
     c_gpu, l_gpu = ctx.neighbours(cap=512)
@@ -48,7 +41,6 @@ def test_neighbour_sets_bit_exact(P, oracle, prec, lanes, scheme, shape):
     c_ref, l_ref = oracle.pairs(pos, rl, cap=512, method="brute")
     assert np.array_equal(c_gpu, c_ref)
     assert sorted_rows(c_gpu, l_gpu) == sorted_rows(c_ref, l_ref)
-    assert ctx.scheme()["scheme"] == ("stencil" if scheme == STENCIL else "lists")
     ctx.close()
 
 
@@ -71,11 +63,10 @@ def ctx_pot(oracle, ctx):
     return oracle.Potential(eps=p.eps, c=p.c, a=p.a, rc=p.rc, n=p.n, m=p.m)
 
 
-@pytest.mark.parametrize("lanes,scheme", [(1, LISTS), (4, LISTS), (16, LISTS), (1, STENCIL),
-                                          (2, STENCIL), (8, STENCIL)])
-def test_forces_mixed(P, oracle, lanes, scheme):
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
+def test_forces_mixed(P, oracle, lanes):
     shape = (6, 5, 7)
-    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes, pair_scheme=scheme)
+    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes)
     pos = on_grid(PI.gaussian_jitter_fcc(shape, 0.1, seed=10 + lanes))
     ctx.set_state(pos, np.zeros_like(pos))
     f, pe, _ = ctx.forces()
@@ -309,7 +300,7 @@ def test_pruned_inner_list_changes_no_result(P, oracle):
     out = []
     for margin in (0.3, -1.0):
         ctx = P.Ctx((8, 7, 9), T0=300.0, seed=12, precision=P.PREC_MIXED, lanes=2,
-                    prune_margin=margin, pair_scheme=LISTS)
+                    prune_margin=margin)
         ctx.apply_strain(2e-3)
         a = ctx.fine_burst(300)
         out.append((ctx.series().copy(), ctx.get_state(), a.prunes))
