@@ -8,7 +8,7 @@ FP64 accumulators) and the coarse-step update.  The metric is atom-steps/s
 (atoms x fine steps per second), whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pta|reference]
-                    [--workload large|plain|batched|uneven|served|precision|profile]
+                    [--workload large|plain|batched|uneven|served|precision|profile|verify]
 
 Under torchrun (N > 1) every rank advances its own specimen (independent
 replicas, no collective on the data path); the time is the maximum over
@@ -63,6 +63,12 @@ WORKLOADS = {
     "precision": dict(name="precision_by_size", n_cells=None, T0=300.0, rate=None, burst=1000,
                       precision=1, count=7,
                       desc="mixed precision vs FP64 per size (10..49 cells), same seed"),
+    "verify": dict(name="verify_fine_dynamics_n20", n_cells=20, T0=300.0, rate=None, burst=2000,
+                   precision=1, count=1,
+                   desc="fine-dynamics verification: 20^3-cell cube (32,000 atoms, 8 nm), loaded "
+                        "to 3.1% strain, then 5 slow jumps of h = 20,000 steps (Delta = 4,000) "
+                        "at 2e-4 strain per jump: one uninterrupted ramped trajectory against "
+                        "PTA with 2,000-step bursts, relative errors per jump"),
     "profile": dict(name="profile_case", n_cells=None, T0=300.0, rate=None, burst=None,
                     precision=1, count=1,
                     desc="one specimen for Nsight Compute captures: --n-cells cube, "
@@ -375,6 +381,31 @@ def run_profile(args, wl):
     return out
 
 
+def run_verify(args, wl):
+    """Sec. Verification with fine dynamics: relative errors of the PTA slow
+    variables against the fine dynamics' measures, per slow jump."""
+    import torch
+    import paper_2603_07321_gb300 as P
+    from paper_2603_07321_gb300.verify import fine_vs_pta
+    P.build()
+    torch.cuda.set_device(0)
+    t = time.perf_counter()
+    out = fine_vs_pta(wl["n_cells"], T0=wl["T0"], seed=1, strain0=0.031, prep_increments=10,
+                      prep_steps=1000, h_steps=20000, delta_steps=4000, n_jumps=5,
+                      burst_steps=wl["burst"], strain_per_jump=2e-4, precision=wl["precision"])
+    dt = time.perf_counter() - t
+    rows = [{"jump": k + 1, "fine_steps": (k + 1) * 20000 + 4000,
+             "error_pct": {"K": 100 * out["errors"][k][0], "U": 100 * out["errors"][k][1],
+                           "T": 100 * out["errors"][k][2]},
+             "v_pta": out["v_pta"][k].tolist(), "v_fine": out["v_fine"][k + 1].tolist(),
+             "source": out["sources"][k]} for k in range(len(out["errors"]))]
+    res = {"workload": wl["name"], "description": wl["desc"], "seconds": dt,
+           "fine_steps": out["fine_steps"], "pta_steps": out["pta_steps"],
+           "v_fine_t0": out["v_fine"][0].tolist(), "rows": rows}
+    print(json.dumps(res), flush=True)
+    return res
+
+
 def run_pta(args, wl):
     import torch
     import paper_2603_07321_gb300 as P
@@ -643,6 +674,8 @@ def main():
         run_precision(args, wl)
     elif args.workload == "profile":
         run_profile(args, wl)
+    elif args.workload == "verify":
+        run_verify(args, wl)
     else:
         run_pta(args, wl)
 

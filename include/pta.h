@@ -233,6 +233,15 @@ int pta_get_strain(const pta_ctx *ctx, double *strain);
  * (which the next burst continues from, Eqs. (x_guess_step1),
  * (x_guess_step3)).  Blocks until the averages are on the host.  nsteps >= 1. */
 int pta_fine_burst(pta_ctx *ctx, int64_t nsteps, pta_averages *out);
+/* Continuous loading (Sec. Verification with fine dynamics): a fine burst
+ * of nsteps steps during which the right grip advances by d_eps_per_step *
+ * L_s along the load axis with every step (with the drift of each step),
+ * instead of being held fixed.  This is the uninterrupted fine dynamics
+ * against which the slow variables of PTA are verified: bursts of it are one
+ * trajectory under a load ramped at d_eps_per_step per step.  The grip
+ * displacement reported by pta_get_strain grows by nsteps * d_eps_per_step.
+ * PTA_EUNSUPPORTED with an adaptive burst length (conv_lag > 0). */
+int pta_ramp_burst(pta_ctx *ctx, int64_t nsteps, double d_eps_per_step, pta_averages *out);
 /* Thermal relaxation before loading (Sec. Boundary conditions): bursts of
  * `window` steps with the right grip free to move along the load axis (its
  * other velocity components stay 0; the left grip stays fixed) until the

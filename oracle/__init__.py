@@ -103,6 +103,9 @@ def _load():
         "or_burst": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_long, ctypes.c_int, dp, dp]),
+        "or_burst_ramp": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_long, ctypes.c_int, ctypes.c_double, dp, dp]),
         "or_burst_relax": (ctypes.c_int, [dp, dp, ctypes.c_long, u8p, potp, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_long, ctypes.c_int, dp, dp]),
@@ -313,18 +316,27 @@ class Specimen:
                                 _ptr(self.flags, ctypes.c_uint8), self.axis, du)
         self.u += du
 
-    def burst(self, nsteps: int, cap: int = 512, relax: bool = False):
+    def burst(self, nsteps: int, cap: int = 512, relax: bool = False, ramp: float = 0.0):
         """Run nsteps of velocity Verlet; returns the series [nsteps, 3] of
         (K eV, U eV, T GPa) sampled after every full step.  relax: the right
-        grip moves freely along the load axis (thermal relaxation)."""
+        grip moves freely along the load axis (thermal relaxation).  ramp:
+        continuous loading, the right grip advances by ramp * L_s (strain
+        units) along the load axis with every step's drift."""
         series = np.zeros((nsteps, 3))
         f = np.zeros((self.n, 3))
-        fn = _load().or_burst_relax if relax else _load().or_burst
-        rc = fn(_ptr(self.pos, ctypes.c_double), _ptr(self.vel, ctypes.c_double),
-                              self.n, _ptr(self.flags, ctypes.c_uint8),
-                              ctypes.byref(self.pot._c()), self.mass, self.dt, self.axis,
-                              self.A0, nsteps, cap, _ptr(series, ctypes.c_double),
-                              _ptr(f, ctypes.c_double))
+        args = (_ptr(self.pos, ctypes.c_double), _ptr(self.vel, ctypes.c_double),
+                self.n, _ptr(self.flags, ctypes.c_uint8), ctypes.byref(self.pot._c()),
+                self.mass, self.dt, self.axis, self.A0, nsteps, cap)
+        outs = (_ptr(series, ctypes.c_double), _ptr(f, ctypes.c_double))
+        if ramp != 0.0:
+            if relax:
+                raise ValueError("a relaxation burst holds no grip to move")
+            du = ramp * self.L_s
+            rc = _load().or_burst_ramp(*args, du, *outs)
+            self.u += nsteps * du
+        else:
+            fn = _load().or_burst_relax if relax else _load().or_burst
+            rc = fn(*args, *outs)
         if rc != 0:
             raise ValueError("neighbour capacity exceeded")
         self.last_forces = f

@@ -622,7 +622,7 @@ OR_API void or_apply_strain(double *pos, long n, const uint8_t *flags, int axis,
  * ------------------------------------------------------------------- */
 static int burst_impl(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
                       double mass, double dt, int axis, double A0, long nsteps, int cap,
-                      double *series, double *f_out, int right_free) {
+                      double *series, double *f_out, int right_free, double grip_du) {
     or_work w;
     w.cap = cap;
     w.counts = (int *)malloc(sizeof(int) * n);
@@ -641,6 +641,10 @@ static int burst_impl(double *pos, double *vel, long n, const uint8_t *flags, co
                 pos[3 * i + d] = pos[3 * i + d] + vel[3 * i + d] * dt;
             }
         }
+        /* continuous loading: the right grip advances by grip_du with the drift */
+        if (grip_du != 0.0)
+            for (long i = 0; i < n; i++)
+                if (flags[i] == 2 && !right_free) pos[3 * i + axis] = pos[3 * i + axis] + grip_du;
         rc = or_forces(pos, n, p, &w);
         if (rc != 0) break;
         for (long i = 0; i < n; i++) {
@@ -663,14 +667,26 @@ static int burst_impl(double *pos, double *vel, long n, const uint8_t *flags, co
 OR_API int or_burst(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
                     double mass, double dt, int axis, double A0, long nsteps, int cap,
                     double *series, double *f_out) {
-    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 0);
+    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 0,
+                      0.0);
+}
+
+/* the same burst with the right grip moving by grip_du along the load axis
+ * at every step (the continuous loading of the fine dynamics against which
+ * PTA is verified, Sec. Verification with fine dynamics) */
+OR_API int or_burst_ramp(double *pos, double *vel, long n, const uint8_t *flags, const or_pot *p,
+                         double mass, double dt, int axis, double A0, long nsteps, int cap,
+                         double grip_du, double *series, double *f_out) {
+    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 0,
+                      grip_du);
 }
 
 /* the same burst with the right grip free along the load axis (relaxation) */
 OR_API int or_burst_relax(double *pos, double *vel, long n, const uint8_t *flags,
                           const or_pot *p, double mass, double dt, int axis, double A0,
                           long nsteps, int cap, double *series, double *f_out) {
-    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 1);
+    return burst_impl(pos, vel, n, flags, p, mass, dt, axis, A0, nsteps, cap, series, f_out, 1,
+                      0.0);
 }
 
 /* state functions of a given state (no time step) */

@@ -223,3 +223,41 @@ def converged_averages(series, lag: int, tol, floor, n_max: int | None = None):
             means.append(sums[q] / float(run))
             counts.append(run)
     return np.array(means), np.array(counts), mask, run
+
+
+# ---------------------------------------------------------------------------
+# Verification with fine dynamics (Sec. Verification with fine dynamics)
+# ---------------------------------------------------------------------------
+def fine_dynamics_measures(specimen, h_steps: int, delta_steps: int, n_jumps: int,
+                           ramp_per_step: float):
+    """v_d^{m,fine}(t_k), k = 0..n_jumps: Eq. (measure) on one uninterrupted
+    fine trajectory under continuous loading (the right grip advances by
+    ramp_per_step * L_s with every step).  The trajectory starts at slow time
+    -Delta; slow time t_k = k h ends at step k h_steps + delta_steps, and the
+    measure is the mean of the state functions over the delta_steps steps
+    ending there (N' = delta_steps samples, no Simpson rule and no restart
+    from guessed initial conditions).  Returns an array [n_jumps + 1, 3]."""
+    out = []
+    for k in range(n_jumps + 1):
+        if k > 0:
+            specimen.burst(h_steps - delta_steps, ramp=ramp_per_step)
+        out.append(specimen.burst(delta_steps, ramp=ramp_per_step).mean(axis=0))
+    return np.array(out)
+
+
+def verification_params(h_steps: int, delta_steps: int, ramp_per_step: float, dt_fs: float = 1.0,
+                        **kw) -> PTAParams:
+    """PTA parameters matching a fine-dynamics verification run: h and Delta
+    are the fine durations h_steps and delta_steps steps (in seconds), the
+    strain rate the ramp's (ramp_per_step per step)."""
+    dt_s = dt_fs * 1e-15
+    return PTAParams(h=h_steps * dt_s, Delta=delta_steps * dt_s,
+                     strain_rate=ramp_per_step / dt_s, **kw)
+
+
+def verification_errors(v_pta, v_fine):
+    """The section's error, |v^PTA_m(t) - v^{m,fine}_d(t)| / |v^{m,fine}_d(t)|
+    (the same form as Eq. (rel_err)), per slow jump and variable."""
+    v_pta = np.asarray(v_pta, dtype=np.float64)
+    v_fine = np.asarray(v_fine, dtype=np.float64)
+    return np.abs(v_pta - v_fine) / np.abs(v_fine)

@@ -25,7 +25,7 @@ __all__ = [
     "pta_apply_strain", "pta_fine_burst", "pta_coarse_step", "pta_get_state", "pta_set_state",
     "pta_forces", "pta_get_neighbours", "pta_get_series", "pta_save_state", "pta_load_state",
     "pta_batch_create", "pta_batch_destroy", "pta_batch_fine_burst", "pta_batch_apply_strain",
-    "pta_batch_coarse_step", "pta_batch_tick", "pta_coarse_update", "pta_footprint_bytes", "PREC_FP64",
+    "pta_batch_coarse_step", "pta_batch_tick", "pta_coarse_update", "pta_ramp_burst", "pta_footprint_bytes", "PREC_FP64",
     "PREC_MIXED",
 ]
 
@@ -131,6 +131,7 @@ _SIGS = {
     "pta_apply_strain": (ctypes.c_int, [_VP, ctypes.c_double]),
     "pta_get_strain": (ctypes.c_int, [_VP, _P(ctypes.c_double)]),
     "pta_fine_burst": (ctypes.c_int, [_VP, ctypes.c_int64, _P(Averages)]),
+    "pta_ramp_burst": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_double, _P(Averages)]),
     "pta_get_series": (ctypes.c_int, [_VP, _P(ctypes.c_double), ctypes.c_int64,
                                       _P(ctypes.c_int64)]),
     "pta_coarse_step": (ctypes.c_int, [_VP, _P(CoarseResult)]),
@@ -322,6 +323,13 @@ def pta_get_strain(h) -> float:
 def pta_fine_burst(h, nsteps: int) -> Averages:
     a = Averages()
     _check(load().pta_fine_burst(h, int(nsteps), ctypes.byref(a)), "pta_fine_burst")
+    return a
+
+
+def pta_ramp_burst(h, nsteps: int, d_eps_per_step: float) -> Averages:
+    a = Averages()
+    _check(load().pta_ramp_burst(h, int(nsteps), float(d_eps_per_step), ctypes.byref(a)),
+           "pta_ramp_burst")
     return a
 
 
@@ -530,6 +538,9 @@ class Ctx:
 
     def fine_burst(self, nsteps):
         return pta_fine_burst(self.h, nsteps)
+
+    def ramp_burst(self, nsteps, d_eps_per_step):
+        return pta_ramp_burst(self.h, nsteps, d_eps_per_step)
 
     def series(self, max_steps=1 << 20):
         return pta_get_series(self.h, max_steps)

@@ -172,14 +172,21 @@ __device__ __forceinline__ void atom_update_mixed(const SpecDev &S, SpecCtl *ctl
     }
     float hh[3] = {hia.x, hia.y, hia.z}, qq[3] = {loa.x, loa.y, loa.z};
     const bool start = (phase == PH_REFRESH) || (done + 1 < nsteps);
-    if (start && moves) {
-        hl_add(v.h.x, v.l.x, kx);
-        hl_add(v.h.y, v.l.y, ky);
-        hl_add(v.h.z, v.l.z, kz);
+    // continuous loading (fine-dynamics verification): a fixed right grip
+    // moves by grip_du along the load axis with every step's drift
+    const float gdu = (start && flag == FLAG_RIGHT && !rfree) ? (float)ctl->grip_du : 0.f;
+    if (start && (moves || gdu != 0.f)) {
         const float dt = S.f_dt;
-        qq[0] += (v.h.x + v.l.x) * dt;
-        qq[1] += (v.h.y + v.l.y) * dt;
-        qq[2] += (v.h.z + v.l.z) * dt;
+        if (moves) {
+            hl_add(v.h.x, v.l.x, kx);
+            hl_add(v.h.y, v.l.y, ky);
+            hl_add(v.h.z, v.l.z, kz);
+            qq[0] += (v.h.x + v.l.x) * dt;
+            qq[1] += (v.h.y + v.l.y) * dt;
+            qq[2] += (v.h.z + v.l.z) * dt;
+        } else {
+            qq[S.axis] += gdu;
+        }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             // move whole grid quanta from lo to hi (both steps exact)

@@ -141,6 +141,12 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
                 x += v.x * S.dt;
                 y += v.y * S.dt;
                 z += v.z * S.dt;
+            } else if (start && flag == FLAG_RIGHT && !rfree && S.ctl->grip_du != 0.0) {
+                // continuous loading (fine-dynamics verification)
+                const double du = S.ctl->grip_du;
+                if (S.axis == 0) x = x + du;
+                else if (S.axis == 1) y = y + du;
+                else z = z + du;
             }
             ((double4_32a *)S.pos[par ^ 1])[a] = make_double4_32a(x, y, z, 0.0);
             ((double4_32a *)S.vel)[a] = v;

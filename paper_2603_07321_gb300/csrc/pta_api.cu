@@ -84,6 +84,7 @@ struct pta_ctx {
     SpecDev *d_self = nullptr;
     double L_s = 0;
     double u = 0;          // grip displacement, A
+    double grip_du = 0;    // host copy of the per-step grip advance of a ramped burst
     bool pta_init = false;
     bool broken = false;
     Runner *solo = nullptr;
@@ -1257,6 +1258,30 @@ int pta_fine_burst(pta_ctx *c, int64_t nsteps, pta_averages *out) {
     pta_averages a;
     int rc = run_burst(r, &nsteps, &a, -1);
     if (rc == PTA_ECUDA) c->broken = true;
+    if (out) *out = a;
+    return rc;
+}
+
+int pta_ramp_burst(pta_ctx *c, int64_t nsteps, double d_eps_per_step, pta_averages *out) {
+    if (!c || nsteps < 1 || !std::isfinite(d_eps_per_step)) return PTA_EINVAL;
+    if (c->par.conv_lag > 0) return PTA_EUNSUPPORTED;  // the ramp needs the whole burst
+    Runner *r;
+    CKR(ctx_solo(c, &r));
+    c->grip_du = d_eps_per_step * c->L_s;
+    CK(cudaMemcpyAsync(&c->hd.ctl->grip_du, &c->grip_du, sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    pta_averages a{};
+    int rc = run_burst(r, &nsteps, &a, -1);
+    if (rc == PTA_ECUDA) {
+        c->broken = true;
+        return rc;
+    }
+    // the grip advanced with every drift of the burst
+    c->u += (double)a.nsteps * c->grip_du;
+    c->grip_du = 0.0;
+    CK(cudaMemcpyAsync(&c->hd.ctl->grip_du, &c->grip_du, sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     if (out) *out = a;
     return rc;
 }

@@ -79,6 +79,8 @@ struct SpecCtl {
     long long conv_n[3];       // adaptive length: step of convergence per variable
     int conv_mask;             // adaptive length: bit m set once variable m converged
     int relax;                 // 1: thermal relaxation, right grip free along the load axis
+    double grip_du;            // continuous loading: the right grip moves this far (A) along
+                               // the load axis with every step (0: held fixed)
     double eval_obs[3];        // K, U, T of the last MODE_EVAL pass
     double mb[8];              // scratch of the Maxwell-Boltzmann set-up
     pta_averages last;         // averages of the last finished burst
