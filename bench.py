@@ -53,13 +53,14 @@ WORKLOADS = {
                          "10/100/300 K, half tension half compression, rates log-uniform "
                          "1e-4..1e-3/s, 3 bursts x 2,000 steps per coarse step, one launch "
                          "set per fine step for all replicas"),
-    "served": dict(name="served_poisson_16req", n_cells=None, T0=None, rate=None, burst=2000,
-                   precision=1, count=16, lanes=1,
-                   desc="first 16 requests of a Poisson trace (mean 2/s): cube side uniform "
-                        "10..49 cells, T0 in 10/100/300 K, rate log-uniform 1e-4..1e-3/s, "
-                        "tension or compression p=0.5, target strain 0.05..0.15, admitted by "
-                        "memory footprint; one bench step = one tick (a coarse step of every "
-                        "live specimen, 3 x 2,000 fine steps)"),
+    "served": dict(name="served_poisson_realtime", n_cells=None, T0=None, rate=None, burst=2000,
+                   precision=1, count=None, lanes=1,
+                   desc="Poisson trace (cube side uniform 10..49 cells, T0 in 10/100/300 K, rate "
+                        "log-uniform 1e-4..1e-3/s, tension or compression p=0.5, target strain "
+                        "0.05..0.15 shortened to at most 4 coarse steps) replayed on the wall "
+                        "clock at ~70% of the measured batched throughput; admission by memory "
+                        "footprint and slots at tick boundaries (continuous batching), 3 x 2,000 "
+                        "fine steps per coarse step"),
     "precision": dict(name="precision_by_size", n_cells=None, T0=300.0, rate=None, burst=1000,
                       precision=1, count=7,
                       desc="mixed precision vs FP64 per size (10..49 cells), same seed"),
@@ -250,71 +251,117 @@ def max_over_ranks(x: float, device="cpu") -> float:
 # own arm
 # ---------------------------------------------------------------------------
 def run_served(args, wl):
-    """Served workload: the request loop of paper_2603_07321_gb300.serve on a
-    Poisson trace; a bench step is one tick of the server."""
+    """Served workload: the request loop of paper_2603_07321_gb300.serve on
+    the Poisson trace replayed in real time at ~70% of the device's measured
+    batched throughput (served_leg); one JSON line with the measured
+    coarse-step, full-curve and queue-wait latencies."""
     import torch
     import paper_2603_07321_gb300 as P
-    from paper_2603_07321_gb300.serve import GPUEngine, Request, Scheduler
-
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     P.build()
-    trace = PI.served_trace(16, seed=7 + rank)
-    reqs = [Request(rid=i, n_cells=r.n_cells, T0=r.T0, seed=r.seed, strain_rate=r.strain_rate,
-                    target_strain=r.target_strain, arrival_s=r.arrival_s,
-                    burst_steps=r.burst_steps, precision=wl["precision"],
-                    lanes=lanes_of(args, wl))
-            for i, r in enumerate(trace)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    cap = batched_leg(P)["value"]
+    res = served_leg(P, capacity=cap, n_requests=args.served_requests)
+    clocks = sampler.stop()
+    out = {"metric": "atom-steps/s", "value": res["value"], "unit": "atom-steps/s",
+           "n_gpus": ws, "steps": res["ticks"], "warmup": 0,
+           "ms_per_step": res["wall_s"] * 1e3 / max(res["ticks"], 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded Poisson request trace, replayed in real time)",
+           "config": {"workload": wl["name"], "description": wl["desc"],
+                      "parallelism": "continuous batching"},
+           "served": res, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def batched_leg(P, steps: int = 1, warmup: int = 1):
+    """The batched ensemble (64 replicas of the 20^3-cell cube, one launch set
+    per fine step for all of them) as a sub-result of the default run:
+    atom-steps/s over `steps` coarse steps after `warmup`."""
+    import torch
+    reqs = PI.config_batched(64, 20)
+    ctxs = [P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=1, burst_steps=r.burst_steps,
+                  strain_rate=r.strain_rate, lanes=1) for r in reqs]
+    b = P.Batch(ctxs)
+    for _ in range(warmup):
+        b.coarse_step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        b.coarse_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    natoms = sum(c.n for c in ctxs)
+    value = natoms * 3 * 2000 * steps / (ms / 1e3)
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "batched_64x_n20", "value": value, "unit": "atom-steps/s",
+            "atoms": natoms, "specimens": len(ctxs), "coarse_steps": steps, "warmup": warmup,
+            "ms_per_coarse_step": ms / steps,
+            "description": WORKLOADS["batched"]["desc"]}
+
+
+def served_leg(P, capacity: float, n_requests: int = 28, utilisation: float = 0.7,
+               max_coarse: int = 4, seed: int = 7, time_cap_s: float = 120.0):
+    """The served workload in real time: the seeded Poisson trace (cube side
+    10..49, T0, rate, sign, target as in the served config) replayed on the
+    wall clock with its arrival rate scaled so that the offered load is
+    `utilisation` of `capacity` (atom-steps/s); each request's curve is
+    shortened to at most `max_coarse` coarse steps so that whole curves
+    finish and their latencies are measured.  Requests are admitted by
+    memory footprint and slots at tick boundaries (continuous batching)."""
+    import torch
+    from paper_2603_07321_gb300.serve import GPUEngine, Request, Scheduler
+    trace = PI.served_trace(n_requests, seed=seed)
+    h = 1.0
+    work, reqs = 0.0, []
+    for i, r in enumerate(trace):
+        n_coarse = int(min(max_coarse, np.ceil(r.target_strain / (abs(r.strain_rate) * h))))
+        target = n_coarse * abs(r.strain_rate) * h
+        work += 4 * r.n_cells ** 3 * 3 * r.burst_steps * (n_coarse + 1)
+        reqs.append(Request(rid=i, n_cells=r.n_cells, T0=r.T0, seed=r.seed,
+                            strain_rate=r.strain_rate, target_strain=target,
+                            arrival_s=r.arrival_s, burst_steps=r.burst_steps, precision=1,
+                            lanes=1))
+    # time-scale the arrivals: offered load = utilisation x capacity
+    span = trace[-1].arrival_s
+    offered_span = work / (utilisation * capacity)
+    scale = offered_span / span
+    for r in reqs:
+        r.arrival_s *= scale
     eng = GPUEngine()
     free, _ = torch.cuda.mem_get_info()
     sched = Scheduler(eng, mem_budget_bytes=int(0.8 * free), max_slots=64)
-    for r in reqs:
-        r.arrival_s = 0.0   # the trace is replayed as fast as the device allows
-        sched.submit(r)
-    for _ in range(args.warmup):
-        sched.tick()
-    torch.cuda.synchronize()
-    steps0 = sum(s["result"].atom_steps for s in sched.live.values()) + \
-        sum(r.atom_steps for r in sched.results.values())
-    lat0 = {rid: len(s["result"].tick_latency_s) for rid, s in sched.live.items()}
-    sampler = ClockSampler(local)
-    sampler.start()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sched.tick()
+    for r in sorted(reqs, key=lambda r: r.arrival_s):
+        sched.submit(r)
+    while (sched.waiting or sched.live) and time.perf_counter() - t0 < time_cap_s:
+        if not sched.tick():
+            nxt = sched.waiting[0].arrival_s if sched.waiting else None
+            if nxt is None:
+                break
+            wait = nxt - sched.now()
+            if wait > 0:
+                time.sleep(min(wait, 0.05))
     torch.cuda.synchronize()
-    dt = max_over_ranks(time.perf_counter() - t0, "cuda")
-    clocks = sampler.stop()
-    steps1 = sum(s["result"].atom_steps for s in sched.live.values()) + \
-        sum(r.atom_steps for r in sched.results.values())
-    lat = [x for rid, s in sched.live.items() for x in s["result"].tick_latency_s[lat0.get(rid, 0):]]
-    natoms = sum(s["req"].n_cells ** 3 * 4 for s in sched.live.values())
-    # coarse steps each request needs to reach its target, at the measured tick time
-    need = [max(1, int(np.ceil(r.target_strain / (abs(r.strain_rate) * 1.0)))) + 1 for r in reqs]
-    tick = float(np.median(lat)) if lat else None
-    out = None
-    if rank == 0:
-        value = (steps1 - steps0) * ws / dt
-        out = {"metric": "atom-steps/s", "value": value, "unit": "atom-steps/s", "n_gpus": ws,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32", "data": "synthetic (seeded Poisson request trace)",
-               "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
-                          "live_specimens": len(sched.live), "parallelism": "continuous batching",
-                          "lanes_per_atom": lanes_of(args, wl) or "automatic"},
-               "served": {"coarse_step_latency_s": {"p50": tick,
-                                                    "p99": float(np.percentile(lat, 99))
-                                                    if lat else None},
-                          "curve_latency_s_projected": {
-                              "p50": float(np.percentile(need, 50)) * tick if tick else None,
-                              "p99": float(np.percentile(need, 99)) * tick if tick else None,
-                              "note": "coarse steps to the target strain x median tick time"}},
-               "clocks": clocks}
-        print(json.dumps(out), flush=True)
+    wall = time.perf_counter() - t0
+    stats = sched.stats()
     eng.close()
     for s in list(sched.live.values()):
         s["handle"].close()
-    return out
+    return {"workload": "served_poisson_realtime", "value": stats["atom_steps"] / wall,
+            "unit": "atom-steps/s", "requests": n_requests, "utilisation_target": utilisation,
+            "capacity_assumed": capacity, "arrival_time_scale": scale,
+            "mean_arrival_rate_per_s": n_requests / (span * scale), "wall_s": wall,
+            "max_coarse_steps_per_curve": max_coarse, **stats}
 
 
 def run_precision(args, wl):
@@ -530,6 +577,25 @@ def run_pta(args, wl):
         e2e = {"value": atom_steps_rank * ws / dt, "unit": "atom-steps/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 3 * 416}
 
+    layout_info = {"lanes": sorted({c.layout()["lanes"] for c in ctxs}),
+                   "source": sorted({c.layout_source for c in ctxs}),
+                   "skin": sorted({c.params.skin for c in ctxs}),
+                   "prune_margin": sorted({c.params.prune_margin for c in ctxs})}
+    # batched and served sub-results (single-GPU default run only)
+    subs = {}
+    if ws == 1 and not args.no_sub and wl["name"].startswith("large"):
+        if batch is not None:
+            batch.close()
+            batch = None
+        for c in ctxs:
+            c.close()
+        ctxs = []
+        torch.cuda.synchronize()
+        subs["batched"] = batched_leg(P)
+        subs["batched"]["gain_over_plain"] = subs["batched"]["value"] / value
+        subs["served"] = served_leg(P, capacity=subs["batched"]["value"])
+        subs["served"]["gain_over_plain"] = subs["served"]["value"] / value
+
     out = None
     if rank == 0:
         cpu = cpu_baseline(wl, reqs[0].n_cells) if (ws == 1 and not args.no_cpu) else None
@@ -548,7 +614,8 @@ def run_pta(args, wl):
             "data": "synthetic (FCC lattice + seeded Maxwell-Boltzmann velocities)",
             "config": {"workload": wl["name"], "description": wl["desc"], "atoms": natoms,
                        "specimens": len(ctxs), "fine_steps_per_step": fine_per_step,
-                       "lanes_per_atom": sorted({c.layout()["lanes"] for c in ctxs}),
+                       "lanes_per_atom": layout_info["lanes"],
+                       "layout": layout_info,
                        "accumulators": "f64", "l2": "working set > 129 MB L2 (no flush)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "k_%s_f32" % dominant[0]
@@ -572,6 +639,7 @@ def run_pta(args, wl):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
+            **subs,
         }
         print(json.dumps(out), flush=True)
     if batch is not None:
@@ -651,6 +719,10 @@ def main():
     ap.add_argument("--impl", default="pta", choices=["pta", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--served-requests", type=int, default=40,
+                    help="requests of the served workload's trace")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the batched and served sub-results of the default run")
     ap.add_argument("--lanes", type=int, default=None,
                     help="threads per atom of every specimen (default: the workload's choice; "
                          "0 = the library's per-specimen choice)")

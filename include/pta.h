@@ -61,8 +61,10 @@ typedef enum {
     PTA_ENAN = -5,            /* a non-finite energy appeared during a burst           */
     PTA_ESTATE = -6,          /* the call is not valid in the context's state          */
     PTA_ERANGE = -7,          /* a coordinate left the range the mixed-precision
-                                 representation holds (|x| < 512 A), or a specimen
-                                 has more than 2^23 atoms                             */
+                                 representation holds (|x| < 512 A), an atom left
+                                 the cell grid (its margin of a quarter of the
+                                 specimen's extent around the lattice), or a
+                                 specimen has more than 2^23 atoms                   */
     PTA_EUNSUPPORTED = -8,    /* an option this build does not provide                 */
     PTA_ECAPACITY = -9        /* the input exceeds the fixed scratch size of
                                  pta_neighbours_noalloc                              */

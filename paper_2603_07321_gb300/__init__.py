@@ -499,8 +499,22 @@ class Ctx:
 
     def __init__(self, n_cells, T0=300.0, seed=1, params: Params | None = None,
                  potential: Potential | None = None, load_axis=2, a0=4.05, grip_width=0.0,
-                 stream=None, **param_kw):
+                 stream=None, tuned: bool = True, replicas: int = 1, **param_kw):
+        """With the threads per atom left automatic (no params, lanes 0 or
+        absent) and `tuned`, the layout the autotuner cached for this size,
+        precision and number of replicas sharing the device (tune.py) is
+        used; without a cache entry the library's own choice."""
         self.spec = make_specimen(n_cells, a0, load_axis, grip_width)
+        self.layout_source = "explicit" if (params is not None or param_kw.get("lanes")) \
+            else "automatic"
+        if params is None and not param_kw.get("lanes") and tuned:
+            from . import tune as _tune
+            nc = (n_cells,) * 3 if np.isscalar(n_cells) else tuple(n_cells)
+            natoms = 4 * int(nc[0]) * int(nc[1]) * int(nc[2])
+            hit = _tune.lookup(natoms, replicas, param_kw.get("precision", PREC_FP64))
+            if hit:
+                param_kw = {**param_kw, **hit}
+                self.layout_source = "tuned"
         self.params = params if params is not None else default_params(**param_kw)
         self.potential = potential if potential is not None else default_potential()
         self.h = pta_create(self.spec, self.potential, T0, seed, self.params, stream)

@@ -4,7 +4,9 @@
 // the squared distance formed as (dx*dx + dy*dy) + dz*dz in FP64 without
 // contraction.  Candidates come from the 27 cells around i's cell on a grid
 // of edge >= rc + skin; atoms outside the grid are clamped onto its border
-// cells, which keeps every pair within reach (clamping is non-expansive).
+// cells, which keeps every pair within reach (clamping is non-expansive), and
+// are reported (PTA_ERANGE): the grid's margin is a quarter of the specimen's
+// extent, which no atom of a deforming specimen reaches.
 // After binning, the atoms themselves are permuted into cell order (cells in
 // rank order, atoms of a cell in creation order), so that
 // the 32 atoms of a warp share a cell and read overlapping neighbours, and a
@@ -54,8 +56,13 @@ __global__ void k_bin(const SpecDev *__restrict__ specs, const int *__restrict__
     double x[3];
     load_pos64(S, par, a, x[0], x[1], x[2]);
     int ci[3];
-    for (int d = 0; d < 3; ++d)
-        ci[d] = clampi((int)floor((x[d] - S.org[d]) * S.inv_h), 0, S.nc[d] - 1);
+    bool out = false;
+    for (int d = 0; d < 3; ++d) {
+        const double q = floor((x[d] - S.org[d]) * S.inv_h);
+        out |= !(q >= 0.0 && q < (double)S.nc[d]);
+        ci[d] = clampi((int)fmax(fmin(q, 1e9), -1e9), 0, S.nc[d] - 1);
+    }
+    if (out) atomicOr(&S.ctl->err, ERR_GRID);
     const int c = cell_rank(S.nc, ci[0], ci[1], ci[2]);
     S.atom_cell[a] = c;
     atomicAdd(&S.cell_cnt[c], 1);

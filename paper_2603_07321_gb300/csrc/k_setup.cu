@@ -437,7 +437,7 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
         int e = c->err;
         r.status = (e & ERR_OVERFLOW) ? PTA_ENEIGH_OVERFLOW
                    : (e & ERR_NAN)    ? PTA_ENAN
-                   : (e & ERR_RANGE)  ? PTA_ERANGE
+                   : (e & (ERR_RANGE | ERR_GRID)) ? PTA_ERANGE
                                       : PTA_OK;
         c->last = r;
         if (slot >= 0 && slot < 3)

@@ -20,12 +20,21 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pta.h"
 #include "pta_dev.cuh"
 
 using namespace pta;
 
 namespace {
+
+// NVTX range over a scope: bursts, ticks, creation and the other host calls
+// show up by name on a profiler timeline (no cost without a profiler)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // CODATA 2018 constants and the unit conversions that follow from them
 constexpr double E_CHARGE = 1.602176634e-19;  // J / eV
@@ -672,6 +681,7 @@ static int runner_upload(Runner *r) {
 }
 
 static int runner_create(pta_ctx *const *members, int k, Runner **out) {
+    Range nv("pta_capture_graphs");
     Runner *r = new (std::nothrow) Runner();
     if (!r) return PTA_ENOMEM;
     r->m.assign(members, members + k);
@@ -752,6 +762,7 @@ static int runner_set_timing(Runner *r, int enable) {
 // bursts of nsteps[i] steps for every member; averages to out (may be NULL);
 // slot >= 0 also files the means for the coarse-step update
 static int run_burst(Runner *r, const int64_t *nsteps, pta_averages *out, int slot) {
+    Range nv("pta_fine_burst");
     const int k = (int)r->m.size();
     for (int i = 0; i < k; ++i) {
         if (r->m[i]->broken) return PTA_ECUDA;
@@ -833,6 +844,7 @@ static int run_strain(Runner *r, const double *d_eps) {
 // coarse-step kernel; `only_init` restricts the tick to members whose
 // initial bursts are still to run (the others idle)
 static int run_tick(Runner *r, pta_coarse_result *out, int only_init) {
+    Range nv(only_init ? "pta_initial_bursts" : "pta_coarse_step");
     const int k = (int)r->m.size();
     std::vector<int> op(k);
     std::vector<int64_t> ns(k);
@@ -1037,6 +1049,7 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
                const pta_params *par, void *stream, pta_ctx **out) {
     if (!out) return PTA_EINVAL;
     *out = nullptr;
+    Range nv("pta_create");
     int rc = validate(spec, pot, par);
     if (rc != PTA_OK) return rc;
     if (!(T0 >= 0) || !std::isfinite(T0)) return PTA_EINVAL;
@@ -1384,6 +1397,7 @@ int pta_set_state(pta_ctx *c, const double *pos, const double *vel, int64_t n) {
 
 int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     if (!c || n != c->hd.n) return PTA_EINVAL;
+    Range nv("pta_forces");
     Runner *r;
     CKR(ctx_solo(c, &r));
     launch_rebuild(r->tab, 1, c->stream);
@@ -1408,6 +1422,7 @@ int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     if (obs)
         for (int q = 0; q < 3; ++q) obs[q] = ctl.eval_obs[q];
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
+    if (ctl.err & ERR_GRID) return PTA_ERANGE;
     return PTA_OK;
 }
 

@@ -27,7 +27,9 @@ constexpr double HI_QUANTUM = 1.0 / 4096.0;
 constexpr double MIXED_RANGE = 511.0;
 
 enum Phase : int { PH_IDLE = 0, PH_REFRESH = 1, PH_RUN = 2 };
-enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4 };
+// ERR_GRID: an atom lay beyond the cell grid's margin at a list build (it is
+// binned onto the nearest border cell, which keeps the pair search complete)
+enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4, ERR_GRID = 8 };
 // mixed precision: velocity as an exact FP32 pair v = h + l
 struct __align__(32) VelHL {
     float4 h, l;

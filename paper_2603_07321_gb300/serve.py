@@ -174,6 +174,9 @@ class Scheduler:
         ticks = [x for r in self.results.values() for x in r.tick_latency_s]
         ticks += [x for s in self.live.values() for x in s["result"].tick_latency_s]
         curves = [r.finished_s - r.arrival_s for r in self.results.values() if r.status == "done"]
+        waits = [r.admitted_s - r.arrival_s for r in self.results.values()
+                 if r.status in ("done", "failed") and math.isfinite(r.admitted_s)]
+        waits += [s["result"].admitted_s - s["result"].arrival_s for s in self.live.values()]
         steps = sum(r.atom_steps for r in self.results.values())
         steps += sum(s["result"].atom_steps for s in self.live.values())
         pct = lambda a, q: float(np.percentile(a, q)) if a else None
@@ -181,6 +184,8 @@ class Scheduler:
                                           "count": len(ticks)},
                 "curve_latency_s": {"p50": pct(curves, 50), "p99": pct(curves, 99),
                                     "count": len(curves)},
+                "queue_wait_s": {"p50": pct(waits, 50), "p99": pct(waits, 99),
+                                 "count": len(waits)},
                 "atom_steps": steps, "ticks": self.ticks,
                 "done": sum(1 for r in self.results.values() if r.status == "done"),
                 "rejected": sum(1 for r in self.results.values() if r.status == "rejected"),
@@ -191,7 +196,7 @@ class GPUEngine:
     """The device side: one pta_ctx per specimen, one pta_batch over the live
     set, rebuilt when the set changes."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, replicas_hint: int = 16):
         from . import (PTAError, Batch, Ctx, default_params, make_specimen,
                        pta_footprint_bytes)
         self._PTAError, self._Batch, self._Ctx = PTAError, Batch, Ctx
@@ -199,6 +204,7 @@ class GPUEngine:
         self.batch = None
         self.batch_members: list = []
         self.stream = stream
+        self.replicas_hint = replicas_hint
 
     def validate(self, req: Request) -> str:
         if req.n_cells < 3 or req.n_cells > 126:
@@ -210,8 +216,15 @@ class GPUEngine:
         return ""
 
     def _p(self, req):
-        return self._params(precision=req.precision, burst_steps=req.burst_steps,
-                            strain_rate=req.strain_rate, lanes=req.lanes)
+        kw = dict(precision=req.precision, burst_steps=req.burst_steps,
+                  strain_rate=req.strain_rate, lanes=req.lanes)
+        if not req.lanes:
+            # the autotuner's layout for this size among ~replicas_hint live specimens
+            from .tune import lookup
+            hit = lookup(4 * req.n_cells ** 3, self.replicas_hint, req.precision)
+            if hit:
+                kw.update(hit)
+        return self._params(**kw)
 
     def footprint(self, req: Request) -> int:
         return int(self._fp(self._spec(req.n_cells), self._p(req)))

@@ -337,3 +337,21 @@ def test_batch_members_match_the_oracle(P, oracle):
     b.close()
     for m in members:
         m.close()
+
+
+def test_atom_beyond_the_cell_grid_is_reported(P, oracle):
+    # the cell grid extends a quarter of the specimen's span beyond the
+    # lattice; an atom placed far outside it (still inside the coordinate
+    # range of the mixed form) makes the burst report PTA_ERANGE
+    for prec in (P.PREC_FP64, P.PREC_MIXED):
+        shape = (5, 5, 5)
+        pos = PI.jittered_fcc(shape, 0.05, seed=3)
+        ctx = P.Ctx(shape, T0=0.0, precision=prec)
+        flags = ctx.flags()
+        i = int(np.flatnonzero(flags == 0)[0])
+        pos[i] = [-150.0, 5.0, 5.0]
+        ctx.set_state(pos, np.zeros_like(pos))
+        with pytest.raises(P.PTAError) as e:
+            ctx.fine_burst(5)
+        assert e.value.status == -7
+        ctx.close()

@@ -167,3 +167,16 @@ def test_bench_lanes_follow_the_workload_unless_overridden():
     assert bench.lanes_of(argparse.Namespace(lanes=None), wl) == 1
     assert bench.lanes_of(argparse.Namespace(lanes=0), wl) == 0
     assert bench.lanes_of(argparse.Namespace(lanes=None), bench.WORKLOADS["large"]) == 0
+
+
+def test_tune_cache_keys_and_round_trip(tmp_path, monkeypatch):
+    monkeypatch.setenv("PTA_TUNE_CACHE", str(tmp_path / "t.json"))
+    from paper_2603_07321_gb300 import tune
+    assert tune.cache_key(32000, 1, 1) == "prec1:atoms32768:replicas1"
+    assert tune.cache_key(470596, 64, 1) == "prec1:atoms524288:replicas64"
+    assert tune.cache_key(470596, 40, 0) == "prec0:atoms524288:replicas64"
+    assert tune.lookup(32000, 1, 1) is None
+    tune.store(32000, 1, 1, {"lanes": 2, "skin": 1.5, "prune_margin": 0.3, "x": 9}, 1e9)
+    assert tune.lookup(32000, 1, 1) == {"lanes": 2, "skin": 1.5, "prune_margin": 0.3}
+    assert tune.lookup(31000, 1, 1) == {"lanes": 2, "skin": 1.5, "prune_margin": 0.3}
+    assert tune.lookup(32000, 64, 1) is None
