@@ -269,8 +269,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                         // position of atom a relative to the centre of cell cc
                         const float ox = ra.x - (float)dx * h, oy = ra.y - (float)dy * h,
                                     oz = ra.z - (float)dz * h;
-                        for (int j = s; j < e; ++j) {
-                            const float4 rj = crec[j];
+                        auto test = [&](int j, const float4 rj) {
                             const float fx = rj.x - ox, fy = rj.y - oy, fz = rj.z - oz;
                             const float r2f = fx * fx + fy * fy + fz * fz;
                             bool in;
@@ -286,7 +285,19 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                                                       code + (unsigned)__float_as_int(rj.w)));
                                 ++cnt;
                             }
+                        };
+                        // four candidates per iteration, their records loaded
+                        // before any is tested; tested in slot order
+                        int j = s;
+                        for (; j + 4 <= e; j += 4) {
+                            const float4 r0 = crec[j], r1 = crec[j + 1], r2 = crec[j + 2],
+                                         r3 = crec[j + 3];
+                            test(j, r0);
+                            test(j + 1, r1);
+                            test(j + 2, r2);
+                            test(j + 3, r3);
                         }
+                        for (; j < e; ++j) test(j, crec[j]);
                     }
                     wr.flush(min(__reduce_min_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 1 << 30),
                                  wr.flushed + RW_ROWS));

@@ -40,13 +40,6 @@ __device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, in
     return (const unsigned *)S.nlist + off;
 }
 
-// displacement of entry e's atom (record x) from the atom's record r0
-__device__ __forceinline__ float3 entry_disp(unsigned e, float4 x, float4 r0, float h, float h8,
-                                             float h64) {
-    return make_float3(fmaf(nl_offx(e), h, x.x - r0.x), fmaf(nl_offy(e), h8, x.y - r0.y),
-                       fmaf(nl_offz(e), h64, x.z - r0.z));
-}
-
 // displacements of two entries from the atom, packed by axis
 __device__ __forceinline__ void entry_disp2(unsigned ea, unsigned eb, float4 xa, float4 xb, float4 r0,
                                             float h, float h8, float h64, float2 &dx, float2 &dy,
@@ -222,12 +215,26 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
     const unsigned *__restrict__ src = (const unsigned *)S.nlist + off;
     unsigned *__restrict__ dst = (unsigned *)S.plist + off;
     const int nn = S.nn[u];
+    const int cl = nn > l ? (nn - l + L - 1) / L : 0;
     int kept = 0;
-    for (int q = 0; q * L + l < nn; ++q) {
-        const unsigned e = __ldg(src + q * 32);
-        const float4 x = __ldg(rel + nl_j(e));
-        const float3 d = entry_disp(e, x, ra, h, h8, h64);
-        if (d.x * d.x + d.y * d.y + d.z * d.z < rp2) dst[(kept++) * 32] = e;
+    // four entries per iteration, the next four words read ahead (the same
+    // spare-iteration rule as the density pass)
+    unsigned e0 = __ldg(src), e1 = __ldg(src + 32), e2 = __ldg(src + 64), e3 = __ldg(src + 96);
+    for (int q = 0; q < cl; q += 4) {
+        const unsigned n0 = __ldg(src + (q + 4) * 32), n1 = __ldg(src + (q + 5) * 32);
+        const unsigned n2 = __ldg(src + (q + 6) * 32), n3 = __ldg(src + (q + 7) * 32);
+        const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
+        const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
+        float2 dx, dy, dz;
+        entry_disp2(e0, e1, x0, x1, ra, h, h8, h64, dx, dy, dz);
+        float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        if (r2.x < rp2) dst[(kept++) * 32] = e0;
+        if (q + 1 < cl && r2.y < rp2) dst[(kept++) * 32] = e1;
+        entry_disp2(e2, e3, x2, x3, ra, h, h8, h64, dx, dy, dz);
+        r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        if (q + 2 < cl && r2.x < rp2) dst[(kept++) * 32] = e2;
+        if (q + 3 < cl && r2.y < rp2) dst[(kept++) * 32] = e3;
+        e0 = n0; e1 = n1; e2 = n2; e3 = n3;
     }
     S.pnn[(long long)u * L + l] = kept;
     if (l == 0) {

@@ -13,10 +13,12 @@ stores the winner in a JSON cache keyed by (precision, atom count rounded to
 a power of two, replica count rounded up to a power of two).  `Ctx` takes
 the cached layout whenever its threads per atom are left automatic.
 
-Every candidate computes the same physics.  Skin and margin leave even the
-summation order unchanged (lists keep every pair within rc in the same
-order), so results are bit-identical; the threads per atom change the order
-in which one atom's pair terms are added (rounding-level differences).
+Every candidate computes the same physics.  The pruning margin leaves the
+summation order unchanged (the inner list keeps every pair within rc in the
+Verlet list's order), so results are bit-identical; the skin changes the cell
+edge and with it the order of each atom's list entries, and the threads per
+atom the order in which one atom's pair terms are added (rounding-level
+differences).
 
     from paper_2603_07321_gb300.tune import tune
     best, table = tune(20, replicas=64)        # measured and cached

@@ -35,31 +35,48 @@ def test_tuner_ranks_the_candidates_it_can_create(cache):
 
 
 def test_tuned_layout_gives_the_same_results(cache):
-    # candidates that differ only in skin and pruning margin: the tuned
-    # layout must give bit-identical forces and trajectories in FP64
+    # the tuned layout computes the same physics: a pruning margin leaves
+    # the summation order as it is (bit-identical, mixed precision); a skin
+    # changes the cell edge h = rc + skin and with it the order of each
+    # atom's list entries, so FP64 results agree to rounding
     P = gpu_package()
     from paper_2603_07321_gb300.tune import tune
     shape = 7
-    auto = P.Ctx(shape, precision=P.PREC_FP64, tuned=False)
-    L = auto.layout()["lanes"]
-    auto.close()
-    best, _ = tune(shape, precision=P.PREC_FP64, lanes=(L,), skins=(1.2, 2.4),
-                   margins=(0.3,), steps=30, warm=10)
     pos = PI.gaussian_jitter_fcc((shape,) * 3, 0.1, seed=4)
-    vel = PI.random_velocities(len(pos), 3e-3, seed=5)
-    out = []
-    for tuned in (True, False):
-        c = P.Ctx(shape, precision=P.PREC_FP64, tuned=tuned)
-        assert c.layout_source == ("tuned" if tuned else "automatic")
+    vel0 = PI.random_velocities(len(pos), 3e-3, seed=5)
+
+    def run(**kw):
+        c = P.Ctx(shape, **kw)
+        vel = vel0.copy()
         vel[c.flags() != 0] = 0.0
         c.set_state(pos, vel)
         f, pe, _ = c.forces()
         c.fine_burst(100)
-        out.append((f, pe, c.series().copy(), c.get_state()[0], c.params.skin))
+        r = (f, pe, c.series().copy(), c.get_state()[0], c.params.skin, c.layout_source)
         c.close()
-    assert out[0][4] == best["skin"]
-    for a, b in zip(out[0][:4], out[1][:4]):
-        assert np.array_equal(a, b)
+        return r
+
+    auto = P.Ctx(shape, precision=P.PREC_MIXED, tuned=False)
+    L = auto.layout()["lanes"]
+    skin = auto.params.skin
+    auto.close()
+    best, _ = tune(shape, precision=P.PREC_MIXED, lanes=(L,), skins=(skin,), margins=(0.2, 0.5),
+                   steps=30, warm=10)
+    a = run(precision=P.PREC_MIXED)
+    b = run(precision=P.PREC_MIXED, tuned=False)
+    assert a[5] == "tuned" and b[5] == "automatic"
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+    best, _ = tune(shape, precision=P.PREC_FP64, lanes=(L,), skins=(1.2, 2.4), margins=(0.3,),
+                   steps=30, warm=10)
+    a = run(precision=P.PREC_FP64)
+    b = run(precision=P.PREC_FP64, tuned=False)
+    assert a[5] == "tuned" and a[4] == best["skin"] and a[4] != b[4]
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12 * np.abs(b[0]).max())
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    np.testing.assert_allclose(a[2], b[2], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(a[3], b[3], rtol=0, atol=1e-9)
 
 
 def test_tuner_for_a_batch_of_replicas(cache):
