@@ -40,6 +40,15 @@ __device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, in
     return (const unsigned *)S.nlist + off;
 }
 
+// one list word: read once per pass, so it skips L1 (the neighbour records
+// keep the space) and asks L2 to fetch the 256-byte block around it, which
+// holds the warp's next row as well
+__device__ __forceinline__ unsigned ld_list(const unsigned *p) {
+    unsigned v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // displacements of two entries from the atom, packed by axis
 __device__ __forceinline__ void entry_disp2(unsigned ea, unsigned eb, float4 xa, float4 xb, float4 r0,
                                             float h, float h8, float h64, float2 &dx, float2 &dy,
@@ -97,10 +106,10 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         if constexpr (L == 1) {
-            unsigned e0 = __ldg(lst), e1 = __ldg(lst + 32), e2 = __ldg(lst + 64), e3 = __ldg(lst + 96);
+            unsigned e0 = ld_list(lst), e1 = ld_list(lst + 32), e2 = ld_list(lst + 64), e3 = ld_list(lst + 96);
             for (int q = 0; q < cl; q += 4) {
-                const unsigned n0 = __ldg(lst + (q + 4) * 32), n1 = __ldg(lst + (q + 5) * 32);
-                const unsigned n2 = __ldg(lst + (q + 6) * 32), n3 = __ldg(lst + (q + 7) * 32);
+                const unsigned n0 = ld_list(lst + (q + 4) * 32), n1 = ld_list(lst + (q + 5) * 32);
+                const unsigned n2 = ld_list(lst + (q + 6) * 32), n3 = ld_list(lst + (q + 7) * 32);
                 const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
                 const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
                 float2 dx, dy, dz;
@@ -113,9 +122,9 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
                 e0 = n0; e1 = n1; e2 = n2; e3 = n3;
             }
         } else {
-            unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
+            unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
             for (int q = 0; q < cl; q += 2) {
-                const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+                const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
                 const float4 xa = __ldg(rel + nl_j(ea));
                 const float4 xb = __ldg(rel + nl_j(eb));
                 float2 dx, dy, dz;
@@ -157,9 +166,9 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
         ra = lf[u];
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
-        unsigned ea = __ldg(lst), eb = __ldg(lst + 32);
+        unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
         for (int q = 0; q < cl; q += 2) {
-            const unsigned na = __ldg(lst + (q + 2) * 32), nb = __ldg(lst + (q + 3) * 32);
+            const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
             const float4 xa = __ldg(lf + nl_j(ea));
             const float4 xb = __ldg(lf + nl_j(eb));
             // the offsets of both entries decoded in packed instructions; the
@@ -219,10 +228,10 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
     int kept = 0;
     // four entries per iteration, the next four words read ahead (the same
     // spare-iteration rule as the density pass)
-    unsigned e0 = __ldg(src), e1 = __ldg(src + 32), e2 = __ldg(src + 64), e3 = __ldg(src + 96);
+    unsigned e0 = ld_list(src), e1 = ld_list(src + 32), e2 = ld_list(src + 64), e3 = ld_list(src + 96);
     for (int q = 0; q < cl; q += 4) {
-        const unsigned n0 = __ldg(src + (q + 4) * 32), n1 = __ldg(src + (q + 5) * 32);
-        const unsigned n2 = __ldg(src + (q + 6) * 32), n3 = __ldg(src + (q + 7) * 32);
+        const unsigned n0 = ld_list(src + (q + 4) * 32), n1 = ld_list(src + (q + 5) * 32);
+        const unsigned n2 = ld_list(src + (q + 6) * 32), n3 = ld_list(src + (q + 7) * 32);
         const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
         const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
         float2 dx, dy, dz;
