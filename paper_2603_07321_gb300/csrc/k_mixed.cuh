@@ -81,25 +81,28 @@ __device__ __forceinline__ float phi_m1(const PotF &P, float r2) {
     return PowF<SC76>::pm(s, P.m) - P.Am + P.Bm * (r2 * ir - P.rc);
 }
 
-// one pair's contribution to the force on the unit's atom and to its pair
-// energy sum: displacement (ex, ey, ez) = r_j - r_i, r2 = |r_j - r_i|^2 < rc^2,
-// fpi + fpj = B'(rho_i) + B'(rho_j)
+// one pair's contribution to the force on the atom and to its pair-energy
+// sums: displacement (ex, ey, ez) = r_j - r_i, r2 = |r_j - r_i|^2 < rc^2,
+// q = w_i + w_j where each record carries w = m a^m B'(rho).  With y = 1/r,
+//   [eps phi_n'(r) + (B'_i + B'_j) phi_m'(r)] / r
+//       = y (eps Bn + q Bm / (m a^m)) - y^2 (eps n a^n y^n + q y^m),
+// and phi_n(r) = a^n y^n + Bn (r + c1) with c1 = -(An / Bn + rc): the pass
+// sums y^n into e7 and r + c1 into er (the constants applied once per atom)
 template <bool SC76>
 __device__ __forceinline__ void force_pair(const PotF &P, float ex, float ey, float ez, float r2,
-                                           float fpij, float &fx, float &fy, float &fz,
-                                           float &en) {
-    const float ir = rsqrt_nr(r2);
-    const float r = r2 * ir;
-    const float s = P.a * ir;
-    float sn, sm;
-    PowF<SC76>::pw(s, P.n, P.m, sn, sm);
-    const float dphn = -(float)P.n * sn * ir + P.Bn;
-    const float dphm = -(float)P.m * sm * ir + P.Bm;
-    const float gg = (P.eps * dphn + fpij * dphm) * ir;
+                                           float q, float &fx, float &fy, float &fz, float &e7,
+                                           float &er) {
+    const float y = rsqrt_nr(r2);
+    float yn, ym;
+    PowF<SC76>::pw(y, P.n, P.m, yn, ym);
+    const float t = fmaf(q, ym, P.kn * yn);
+    const float c = fmaf(q, P.bmq, P.ebn);
+    const float gg = y * fmaf(-y, t, c);
     fx += gg * ex;
     fy += gg * ey;
     fz += gg * ez;
-    en += sn - P.An + P.Bn * (r - P.rc);
+    e7 += yn;
+    er += fmaf(r2, y, P.c1);
 }
 
 // (h, l) += d exactly up to the final renormalisation: Knuth's two-sum of h
@@ -115,8 +118,8 @@ __device__ __forceinline__ void hl_add(float &h, float &l, float d) {
     h = hh;
 }
 
-// After the force pass of atom a (compact slot; force f, pair-energy sum en,
-// F'(rho_a) = fpa): its energy, its share of the reaction, and the
+// After the force pass of atom a (compact slot; force f, pair-energy sum
+// en = sum_j phi_n(r_aj), record weight fpa = m a^m B'(rho_a)): its energy, its share of the reaction, and the
 // velocity-Verlet update -- the half-kick that finishes the step (phase RUN),
 // the sample of K, and unless the burst ends the half-kick and drift of the
 // next step; the new position (hi + lo, whole grid quanta moved from lo to
@@ -131,7 +134,7 @@ __device__ __forceinline__ void atom_update_mixed(const SpecDev &S, SpecCtl *ctl
                                                   double &ke, double &pe, double &rr, float &d2,
                                                   float &dp2) {
     const float eps = S.pot.f_eps;
-    const float pe_a = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2h / fpa : 0.f);
+    const float pe_a = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2hq / fpa : 0.f);
     pe += (double)pe_a;
     const uint8_t flag = S.flags[a];
     if (flag == FLAG_RIGHT) rr -= (double)(S.axis == 0 ? fx : (S.axis == 1 ? fy : fz));

@@ -12,7 +12,8 @@
 // in entry order.
 //
 // Pass 1 (density): rho_i = sum_j phi_m(r_ij), then B'(rho_i) =
-// -eps c / (2 sqrt(rho_i)) stored beside the record.  Eq. (pe).
+// -eps c / (2 sqrt(rho_i)), stored beside the record scaled by m a^m (the
+// force pass's pair terms are arranged around that weight).  Eq. (pe).
 // Pass 2 (force):   F_i = sum_j [eps phi_n'(r) + (B'_i + B'_j) phi_m'(r)] (r_j - r_i)/r,
 // Eq. (f_int), the per-atom energy 1/2 eps sum_j phi_n + B(rho_i), and the
 // velocity-Verlet update fused behind it (atom_update_mixed).  Grip atoms
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
     }
     rho = lane_sum<L>(rho);
     if (valid && l == 0) {
-        const float fp = rho > 0.f ? -0.5f * P.ec * rsqrtf(rho) : 0.f;
+        // w = m a^m B'(rho), B'(rho) = -eps c / (2 sqrt(rho))
+        const float fp = rho > 0.f ? P.fpsc * rsqrtf(rho) : 0.f;
         ((float4 *)S.posfp)[u] = make_float4(ra.x, ra.y, ra.z, fp);
     }
 }
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
     const float4 *__restrict__ lf = (const float4 *)S.posfp;
     const float h = S.f_q, h8 = S.f_q8, h64 = S.f_q64;
     const float rc2 = P.rc2;
-    float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e7 = 0.f, er = 0.f;
     float4 ra = make_float4(0, 0, 0, 0);
     if (valid) {
         ra = lf[u];
@@ -176,10 +178,10 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
             float2 dx, dy, dz;
             entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
             const float r2a = dx.x * dx.x + dy.x * dy.x + dz.x * dz.x;
-            if (r2a < rc2) force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, en);
+            if (r2a < rc2) force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, e7, er);
             const float r2b = dx.y * dx.y + dy.y * dy.y + dz.y * dz.y;
             if (q + 1 < cl && r2b < rc2)
-                force_pair<SC76>(P, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, en);
+                force_pair<SC76>(P, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, e7, er);
             ea = na;
             eb = nb;
         }
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
     fx = lane_sum<L>(fx);
     fy = lane_sum<L>(fy);
     fz = lane_sum<L>(fz);
-    en = lane_sum<L>(en);
+    const float en = lane_sum<L>(P.an * e7 + P.Bn * er);
     double ke = 0.0, pe = 0.0, rr = 0.0;
     float d2 = 0.f, dp2 = 0.f;
     if (valid && l == 0)

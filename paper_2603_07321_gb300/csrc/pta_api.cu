@@ -260,7 +260,7 @@ static PotDev make_pot(const pta_potential &p) {
     d.f_Am = (float)d.Am;
     d.f_Bm = (float)d.Bm;
     d.f_ec = (float)d.ec;
-    d.f_ec2h = (float)(0.5 * d.ec * d.ec);
+    d.f_ec2hq = (float)(0.5 * d.ec * d.ec * p.m * hpow(p.a, p.m));
     d.sc76 = (p.n == 7 && p.m == 6) ? 1 : 0;
     return d;
 }
@@ -601,6 +601,16 @@ static int runner_upload(Runner *r) {
         pf.Bn = s.pot.f_Bn;
         pf.eps = s.pot.f_eps;
         pf.ec = s.pot.f_ec;
+        {
+            const PotDev &q = s.pot;
+            const double amm = q.m * hpow(q.a, q.m);
+            pf.an = (float)hpow(q.a, q.n);
+            pf.kn = (float)(q.eps * q.n * hpow(q.a, q.n));
+            pf.bmq = (float)(q.Bm / amm);
+            pf.ebn = (float)(q.eps * q.Bn);
+            pf.c1 = (float)(-(q.An / q.Bn + q.rc));
+            pf.fpsc = (float)(-0.5 * q.ec * amm);
+        }
         pf.n = s.pot.n;
         pf.m = s.pot.m;
         const int g = group_of({s.prec, s.L, s.pot.sc76, pf});

@@ -43,7 +43,8 @@ enum AtomFlag : uint8_t { FLAG_MOBILE = 0, FLAG_LEFT = 1, FLAG_RIGHT = 2 };
 struct PotDev {
     double eps, c, a, rc, rc2, An, Bn, Am, Bm, ec;
     int n, m;
-    float f_eps, f_a, f_rc, f_rc2, f_An, f_Bn, f_Am, f_Bm, f_ec, f_ec2h;
+    float f_eps, f_a, f_rc, f_rc2, f_An, f_Bn, f_Am, f_Bm, f_ec;
+    float f_ec2hq;  // (eps c)^2 m a^m / 2: B(rho) = f_ec2hq / w with w = m a^m B'(rho)
     int sc76;  // 1 when (n, m) == (7, 6): the fast specialised kernels apply
 };
 
@@ -52,6 +53,13 @@ struct PotDev {
 // no load and no register inside the pair loops
 struct PotF {
     float a, rc, rc2, Am, Bm, An, Bn, eps, ec;
+    // force pass (the record's fourth component is w = m a^m B'(rho)):
+    float an;    // a^n
+    float kn;    // eps n a^n
+    float bmq;   // Bm / (m a^m)
+    float ebn;   // eps Bn
+    float c1;    // -(An / Bn + rc): phi_n(r) = a^n r^-n + Bn (r + c1)
+    float fpsc;  // -eps c m a^m / 2: w = fpsc / sqrt(rho) (density pass)
     int n, m;
 };
 
