@@ -61,16 +61,16 @@ __device__ __forceinline__ float2 rsqrt2_nr(float2 r2) {
     return __ffma2_rn(__fmul2_rn(y, f2(-0.5f)), e, y);
 }
 
-// phi_m of two pairs at once (squared distances r2), for the density sum;
-// the caller adds the halves whose r2 is below rc^2, in order
+// phi_m of two pairs at once (squared distances r2), for the density sum:
+// with y = 1/r, phi_m = (a^m y^m - Am) + Bm (r - rc); the caller adds the
+// halves whose r2 is below rc^2, in order
 __device__ __forceinline__ float2 phi_m2_sc76(const PotF &P, float2 r2) {
-    const float2 ir = rsqrt2_nr(r2);
-    const float2 s = __fmul2_rn(f2(P.a), ir);
-    const float2 s2 = __fmul2_rn(s, s);
-    const float2 s3 = __fmul2_rn(s2, s);
-    const float2 s6 = __fmul2_rn(s3, s3);
-    const float2 u = __fadd2_rn(__fmul2_rn(r2, ir), f2(-P.rc));
-    return __ffma2_rn(f2(P.Bm), u, __fadd2_rn(s6, f2(-P.Am)));
+    const float2 y = rsqrt2_nr(r2);
+    const float2 y2 = __fmul2_rn(y, y);
+    const float2 y3 = __fmul2_rn(y2, y);
+    const float2 y6 = __fmul2_rn(y3, y3);
+    const float2 u = __ffma2_rn(r2, y, f2(-P.rc));
+    return __ffma2_rn(f2(P.Bm), u, __ffma2_rn(f2(P.am), y6, f2(-P.Am)));
 }
 
 // phi_m of one pair (r2 < rc^2)

@@ -605,6 +605,7 @@ static int runner_upload(Runner *r) {
             const PotDev &q = s.pot;
             const double amm = q.m * hpow(q.a, q.m);
             pf.an = (float)hpow(q.a, q.n);
+            pf.am = (float)hpow(q.a, q.m);
             pf.kn = (float)(q.eps * q.n * hpow(q.a, q.n));
             pf.bmq = (float)(q.Bm / amm);
             pf.ebn = (float)(q.eps * q.Bn);

@@ -55,6 +55,7 @@ struct PotF {
     float a, rc, rc2, Am, Bm, An, Bn, eps, ec;
     // force pass (the record's fourth component is w = m a^m B'(rho)):
     float an;    // a^n
+    float am;    // a^m (density pass)
     float kn;    // eps n a^n
     float bmq;   // Bm / (m a^m)
     float ebn;   // eps Bn
