@@ -70,6 +70,11 @@ WORKLOADS = {
                         "to 3.1% strain, then 5 slow jumps of h = 20,000 steps (Delta = 4,000) "
                         "at 2e-4 strain per jump: one uninterrupted ramped trajectory against "
                         "PTA with 2,000-step bursts, relative errors per jump"),
+    "peaks": dict(name="op_rates", n_cells=None, T0=None, rate=None, burst=None, precision=1,
+                  count=1,
+                  desc="the probe's rates: FMA (FP32, packed FP32, FP64) and the operations "
+                       "a pair pass evaluating each unordered pair once would add per pair for "
+                       "deterministic 64-bit fixed-point j-side sums"),
     "profile": dict(name="profile_case", n_cells=None, T0=300.0, rate=None, burst=None,
                     precision=1, count=1,
                     desc="one specimen for Nsight Compute captures: --n-cells cube, "
@@ -428,6 +433,46 @@ def run_profile(args, wl):
     return out
 
 
+def measure_op_rates(P, target_ms: float = 100.0):
+    """Rates (G operations/s) of the probe's kinds 3-5: 64-bit integer
+    reductions to global memory at scattered addresses, 64-bit shared-memory
+    atomic adds, FP32 -> int64 conversions."""
+    out = {}
+    for kind, name in ((3, "red_global_u64"), (4, "atom_shared_u64"), (5, "cvt_f32_s64")):
+        it = 64
+        P.pta_measure_fma_rate(kind, it)
+        ops, ms = P.pta_measure_fma_rate(kind, it)
+        it = max(it, int(it * target_ms / max(ms, 1e-3)))
+        ops, ms = P.pta_measure_fma_rate(kind, it)
+        out[name] = ops / (ms / 1e3) / 1e9
+    return out
+
+
+def run_peaks(args, wl):
+    """The probe's rates, and what they mean for a force pass that evaluates
+    each unordered pair once with deterministic (64-bit fixed-point) j-side
+    sums of F_x, F_y, F_z and the pair energy: four conversions and four
+    reductions per pair, against the full-list pass's two evaluations."""
+    import torch
+    import paper_2603_07321_gb300 as P
+    P.build()
+    torch.cuda.set_device(0)
+    fma = measure_fma_peaks(P)
+    ops = measure_op_rates(P)
+    pairs = perfect_lattice_pairs(49)
+    per_pair = 4  # F_x, F_y, F_z, pair energy
+    out = {"workload": wl["name"], "description": wl["desc"],
+           "sm_count": torch.cuda.get_device_properties(0).multi_processor_count,
+           "fma_tflops": fma, "ops_gops": ops,
+           "newton3_force_pass_floor_us": {
+               "pairs": pairs,
+               "j_side_reductions_global": pairs * per_pair / (ops["red_global_u64"] * 1e9) * 1e6,
+               "j_side_atomics_shared": pairs * per_pair / (ops["atom_shared_u64"] * 1e9) * 1e6,
+               "conversions": pairs * per_pair / (ops["cvt_f32_s64"] * 1e9) * 1e6}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def run_verify(args, wl):
     """Sec. Verification with fine dynamics: relative errors of the PTA slow
     variables against the fine dynamics' measures, per slow jump."""
@@ -746,6 +791,8 @@ def main():
         run_precision(args, wl)
     elif args.workload == "profile":
         run_profile(args, wl)
+    elif args.workload == "peaks":
+        run_peaks(args, wl)
     elif args.workload == "verify":
         run_verify(args, wl)
     else:

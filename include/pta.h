@@ -354,7 +354,15 @@ int pta_batch_get_timing(pta_batch *batch, pta_kernel_times *out);
  * chains of `iters` steps; kind 0 = scalar FP32, 1 = packed FP32 (two
  * lanes per instruction), 2 = FP64.  *flops gets the flop count (2 per FMA
  * and lane), *ms the launch's CUDA-event time on `stream` (a cudaStream_t).
- * Blocks until the launch is done. */
+ * Kinds 3-5 time the operations a pair pass that evaluates each unordered
+ * pair once would add per pair to keep 64-bit fixed-point (deterministic)
+ * j-side sums: 3 = 64-bit integer reductions to global memory at hashed
+ * addresses of a 15 MB buffer (allocated and freed by the call, as is a
+ * small buffer every kind's keep-alive stores go to), 4 = 64-bit
+ * integer atomic adds in shared memory, 5 = FP32 -> int64 conversions
+ * (16 per iteration and thread); for these *flops gets the operation count.
+ * Returns PTA_EINVAL for another kind or iters < 1.  Blocks until the launch
+ * is done. */
 int pta_measure_fma_rate(int kind, int64_t iters, void *stream, double *flops, double *ms);
 
 /* Neighbour lists without device allocation.

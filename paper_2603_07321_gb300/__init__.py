@@ -456,7 +456,9 @@ def pta_batch_get_timing(b) -> KernelTimes:
 
 def pta_measure_fma_rate(kind: int, iters: int, stream=None):
     """(flops, ms) of one launch of FMA chains: kind 0 scalar FP32, 1 packed
-    FP32, 2 FP64."""
+    FP32, 2 FP64; or (operations, ms) of kind 3 (64-bit integer reductions to
+    global memory), 4 (64-bit shared-memory atomic adds), 5 (FP32 -> int64
+    conversions)."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream

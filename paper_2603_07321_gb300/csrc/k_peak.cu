@@ -4,6 +4,13 @@
 // the launch is bound by the FMA units alone; flops = 2 x FMAs.  Three
 // forms: scalar FP32, packed FP32 (two lanes per instruction, the form the
 // density pass uses) and FP64.
+//
+// Three more forms time the operations that a pair pass evaluating each
+// unordered pair once (Newton's third law) would add per pair to keep its
+// sums deterministic, the j-side sums held in 64-bit fixed point (integer
+// addition is associative): 64-bit integer reductions to global memory at
+// scattered addresses, 64-bit integer atomic adds in shared memory, and
+// FP32 -> int64 conversions.  Their counts are operations, not flops.
 #include <cuda_runtime.h>
 
 #include "pta.h"
@@ -60,14 +67,63 @@ __global__ void __launch_bounds__(PEAK_TPB) k_fma_f64(long long iters, double a,
     if (s == 1234.5678) out[blockIdx.x] = (float)s;
 }
 
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// per thread `iters` reductions, each to a hashed slot of buf (nslot slots)
+__global__ void __launch_bounds__(PEAK_TPB) k_red_u64(long long iters,
+                                                      unsigned long long *buf, unsigned nslot) {
+    const unsigned t = blockIdx.x * PEAK_TPB + threadIdx.x;
+    for (long long i = 0; i < iters; ++i) {
+        const unsigned s = mix32(t * 0x9e3779b9u + (unsigned)i) % nslot;
+        asm volatile("red.global.add.u64 [%0], %1;" ::"l"(buf + s), "l"(1ull) : "memory");
+    }
+}
+
+constexpr int SH_SLOTS = 4096;
+
+__global__ void __launch_bounds__(PEAK_TPB) k_atom_shared_u64(long long iters, float *out) {
+    __shared__ unsigned long long sh[SH_SLOTS];
+    for (int i = threadIdx.x; i < SH_SLOTS; i += PEAK_TPB) sh[i] = 0;
+    __syncthreads();
+    const unsigned t = blockIdx.x * PEAK_TPB + threadIdx.x;
+    for (long long i = 0; i < iters; ++i)
+        atomicAdd(&sh[mix32(t * 0x9e3779b9u + (unsigned)i) & (SH_SLOTS - 1)], 1ull);
+    __syncthreads();
+    if (sh[threadIdx.x] == 123456789ull) out[blockIdx.x] = 1.f;  // keeps the adds alive
+}
+
+__global__ void __launch_bounds__(PEAK_TPB) k_cvt_f32_s64(long long iters, float a, float *out) {
+    float x[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) x[c] = (float)(threadIdx.x + c) * 1e-3f;
+    long long acc = 0;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            acc += __float2ll_rn(x[c]);
+            x[c] += a;
+        }
+    }
+    if (acc == 123456789ll) out[blockIdx.x] = 1.f;
+}
+
 }  // namespace
 
 extern "C" int pta_measure_fma_rate(int kind, int64_t iters, void *stream, double *flops,
                                     double *ms) {
-    if (kind < 0 || kind > 2 || iters < 1 || !flops || !ms) return PTA_EINVAL;
+    if (kind < 0 || kind > 5 || iters < 1 || !flops || !ms) return PTA_EINVAL;
     int dev = 0, nsm = 0, per_sm = 0;
-    const void *fn = kind == 0 ? (const void *)k_fma_f32
-                               : (kind == 1 ? (const void *)k_fma_f32x2 : (const void *)k_fma_f64);
+    const void *fns[6] = {(const void *)k_fma_f32,        (const void *)k_fma_f32x2,
+                          (const void *)k_fma_f64,        (const void *)k_red_u64,
+                          (const void *)k_atom_shared_u64, (const void *)k_cvt_f32_s64};
+    const void *fn = fns[kind];
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PEAK_TPB, 0) != cudaSuccess ||
@@ -78,26 +134,59 @@ extern "C" int pta_measure_fma_rate(int kind, int64_t iters, void *stream, doubl
     cudaStream_t st = (cudaStream_t)stream;
     // exactly one wave of resident blocks: every SM full, no tail
     const int blocks = nsm * per_sm;
+    // reduction targets: 4 slots per atom of a 470,596-atom specimen (15 MB,
+    // resident in L2 like the force sums of such a pass would be)
+    const unsigned nslot = 470596u * 4u;
+    unsigned long long *buf = nullptr;
+    float *sink = nullptr;  // one float per block: the kernels' keep-alive stores
+    if (cudaMalloc(&sink, 4ull * blocks) != cudaSuccess ||
+        (kind == 3 && cudaMalloc(&buf, 8ull * nslot) != cudaSuccess)) {
+        if (sink) cudaFree(sink);
+        cudaGetLastError();
+        return PTA_ENOMEM;
+    }
+    if (kind == 3 && cudaMemsetAsync(buf, 0, 8ull * nslot, st) != cudaSuccess) {
+        cudaFree(buf);
+        cudaFree(sink);
+        cudaGetLastError();
+        return PTA_ECUDA;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (buf) cudaFree(buf);
+        cudaFree(sink);
         cudaGetLastError();
         return PTA_ECUDA;
     }
     cudaEventRecord(e0, st);
     if (kind == 0)
-        k_fma_f32<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999f, 1e-7f, nullptr);
+        k_fma_f32<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999f, 1e-7f, sink);
     else if (kind == 1)
-        k_fma_f32x2<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999f, 1e-7f, nullptr);
+        k_fma_f32x2<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999f, 1e-7f, sink);
+    else if (kind == 2)
+        k_fma_f64<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999, 1e-7, sink);
+    else if (kind == 3)
+        k_red_u64<<<blocks, PEAK_TPB, 0, st>>>(iters, buf, nslot);
+    else if (kind == 4)
+        k_atom_shared_u64<<<blocks, PEAK_TPB, 0, st>>>(iters, sink);
     else
-        k_fma_f64<<<blocks, PEAK_TPB, 0, st>>>(iters, 0.999999, 1e-7, nullptr);
+        k_cvt_f32_s64<<<blocks, PEAK_TPB, 0, st>>>(iters, 1.1e-3f, sink);
     cudaEventRecord(e1, st);
     float t = 0.f;
     const cudaError_t e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (buf) cudaFree(buf);
+    cudaFree(sink);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return PTA_ECUDA;
-    *flops = 2.0 * (double)blocks * PEAK_TPB * (double)iters * NCH;
+    const double threads = (double)blocks * PEAK_TPB;
+    if (kind <= 2)
+        *flops = 2.0 * threads * (double)iters * NCH;
+    else if (kind == 5)
+        *flops = threads * (double)iters * NCH;
+    else
+        *flops = threads * (double)iters;
     *ms = t;
     return PTA_OK;
 }
