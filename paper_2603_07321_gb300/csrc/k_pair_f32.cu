@@ -25,7 +25,7 @@ namespace pta {
 
 // The entry loop is unrolled by two (by four in the density pass); the next
 // two (four) entries are read before the current ones are evaluated.  Those
-// reads go past an atom's count into the eight spare iterations every list
+// reads go past an atom's count into the sixteen spare iterations every list
 // keeps, whose entries are valid indices, so the loop carries no bounds tests.
 
 // the entries lane l of atom u reads (the inner list when pruning is on, else
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
 // distances tested against (rc + margin)^2 widened by 1e-5).  Pairs within
 // rc are therefore all kept, in the order the lane sums them.
 template <int L>
-__global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict__ specs,
+__global__ void __launch_bounds__(TPB, 7) k_prune_f32(const SpecDev *__restrict__ specs,
                                                       const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
     if (S.prec == PTA_PREC_FP64 || !prune_active(S, force)) return;
@@ -228,24 +228,28 @@ __global__ void __launch_bounds__(TPB, 8) k_prune_f32(const SpecDev *__restrict_
     const int nn = S.nn[u];
     const int cl = nn > l ? (nn - l + L - 1) / L : 0;
     int kept = 0;
-    // four entries per iteration, the next four words read ahead (the same
-    // spare-iteration rule as the density pass)
-    unsigned e0 = ld_list(src), e1 = ld_list(src + 32), e2 = ld_list(src + 64), e3 = ld_list(src + 96);
-    for (int q = 0; q < cl; q += 4) {
-        const unsigned n0 = ld_list(src + (q + 4) * 32), n1 = ld_list(src + (q + 5) * 32);
-        const unsigned n2 = ld_list(src + (q + 6) * 32), n3 = ld_list(src + (q + 7) * 32);
-        const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
-        const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
-        float2 dx, dy, dz;
-        entry_disp2(e0, e1, x0, x1, ra, h, h8, h64, dx, dy, dz);
-        float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        if (r2.x < rp2) dst[(kept++) * 32] = e0;
-        if (q + 1 < cl && r2.y < rp2) dst[(kept++) * 32] = e1;
-        entry_disp2(e2, e3, x2, x3, ra, h, h8, h64, dx, dy, dz);
-        r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        if (q + 2 < cl && r2.x < rp2) dst[(kept++) * 32] = e2;
-        if (q + 3 < cl && r2.y < rp2) dst[(kept++) * 32] = e3;
-        e0 = n0; e1 = n1; e2 = n2; e3 = n3;
+    // eight entries per iteration (eight gathers in flight), the next eight
+    // words read ahead: rows up to cl + 14, within the spare iterations
+    unsigned e[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e[k] = ld_list(src + k * 32);
+    for (int q = 0; q < cl; q += 8) {
+        unsigned nx[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) nx[k] = ld_list(src + (q + 8 + k) * 32);
+        float4 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __ldg(rel + nl_j(e[k]));
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            float2 dx, dy, dz;
+            entry_disp2(e[k], e[k + 1], x[k], x[k + 1], ra, h, h8, h64, dx, dy, dz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            if (q + k < cl && r2.x < rp2) dst[(kept++) * 32] = e[k];
+            if (q + k + 1 < cl && r2.y < rp2) dst[(kept++) * 32] = e[k + 1];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) e[k] = nx[k];
     }
     S.pnn[(long long)u * L + l] = kept;
     if (l == 0) {

@@ -312,10 +312,11 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
         const double nb = 4.0 / 3.0 * 3.141592653589793 * rl * rl * rl * dens;
         z->cap_use = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
     }
-    // eight spare iterations per atom: the pair loops read up to four
-    // entries ahead without bounds tests (spare entries hold earlier, valid
+    // sixteen spare iterations per atom: the pair loops read up to eight
+    // entries ahead and the pruning up to fifteen, without bounds tests
+    // (spare entries hold earlier, valid
     // indices or 0)
-    z->cap = z->cap_use + 8 * z->L;
+    z->cap = z->cap_use + 16 * z->L;
     z->nblk_pair = (int)((z->n * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
     // cell edge a multiple of 2^-11 A and grid origin on the 2^-12 A grid, so
