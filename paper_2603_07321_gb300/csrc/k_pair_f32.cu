@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
 }
 
 template <int L, bool SC76>
-__global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict__ specs,
+__global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict__ specs,
                                                       const int *__restrict__ b2s, int mode,
                                                       const PotF P) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -168,22 +168,40 @@ __global__ void __launch_bounds__(TPB, 9) k_force_f32(const SpecDev *__restrict_
         ra = lf[u];
         int cl;
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
-        unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
-        for (int q = 0; q < cl; q += 2) {
-            const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
-            const float4 xa = __ldg(lf + nl_j(ea));
-            const float4 xb = __ldg(lf + nl_j(eb));
-            // the offsets of both entries decoded in packed instructions; the
-            // pair terms stay scalar (packed, they measured slower here)
+        // the offsets of two entries decoded in packed instructions; the pair
+        // terms stay scalar (packed, they measured slower here)
+        auto two = [&](unsigned ea, unsigned eb, float4 xa, float4 xb, bool va, bool vb) {
             float2 dx, dy, dz;
             entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
             const float r2a = dx.x * dx.x + dy.x * dy.x + dz.x * dz.x;
-            if (r2a < rc2) force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, e7, er);
+            if (va && r2a < rc2)
+                force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, e7, er);
             const float r2b = dx.y * dx.y + dy.y * dy.y + dz.y * dz.y;
-            if (q + 1 < cl && r2b < rc2)
+            if (vb && r2b < rc2)
                 force_pair<SC76>(P, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, e7, er);
-            ea = na;
-            eb = nb;
+        };
+        if constexpr (L == 1) {
+            unsigned e0 = ld_list(lst), e1 = ld_list(lst + 32), e2 = ld_list(lst + 64),
+                     e3 = ld_list(lst + 96);
+            for (int q = 0; q < cl; q += 4) {
+                const unsigned n0 = ld_list(lst + (q + 4) * 32), n1 = ld_list(lst + (q + 5) * 32);
+                const unsigned n2 = ld_list(lst + (q + 6) * 32), n3 = ld_list(lst + (q + 7) * 32);
+                const float4 x0 = __ldg(lf + nl_j(e0)), x1 = __ldg(lf + nl_j(e1));
+                const float4 x2 = __ldg(lf + nl_j(e2)), x3 = __ldg(lf + nl_j(e3));
+                two(e0, e1, x0, x1, true, q + 1 < cl);
+                if (q + 2 < cl) two(e2, e3, x2, x3, true, q + 3 < cl);
+                e0 = n0; e1 = n1; e2 = n2; e3 = n3;
+            }
+        } else {
+            unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
+            for (int q = 0; q < cl; q += 2) {
+                const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
+                const float4 xa = __ldg(lf + nl_j(ea));
+                const float4 xb = __ldg(lf + nl_j(eb));
+                two(ea, eb, xa, xb, true, q + 1 < cl);
+                ea = na;
+                eb = nb;
+            }
         }
     }
     fx = lane_sum<L>(fx);
