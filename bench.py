@@ -88,18 +88,30 @@ WORKLOADS = {
 
 
 
+PAIR_SOURCES = ("k_pair_f32.cu", "k_mixed.cuh", "k_pair_common.cuh", "pta_dev.cuh")
+
+
+def pair_source_sha() -> str:
+    """First 16 hex digits of the SHA-256 of the mixed-precision pair kernels'
+    sources (concatenated in PAIR_SOURCES order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in PAIR_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_07321_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def captured_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed Nsight Compute
     summary, or None when the summary is missing or the kernel's source has
     changed since it was captured."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
-    src = os.path.join(ROOT, "paper_2603_07321_gb300", "csrc", "k_pair_f32.cu")
     try:
         txt = open(path).read()
         vals = dict(line.split(": ", 1) for line in txt.splitlines()
                     if line.startswith(("dram_bytes_per_launch:", "kernel_source_sha256_16:")))
-        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        cur = pair_source_sha()
         if vals.get("kernel_source_sha256_16", "").strip() != cur:
             return None
         return int(vals["dram_bytes_per_launch"])
