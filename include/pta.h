@@ -66,8 +66,12 @@ typedef enum {
                                  specimen's extent around the lattice), or a
                                  specimen has more than 2^23 atoms                   */
     PTA_EUNSUPPORTED = -8,    /* an option this build does not provide                 */
-    PTA_ECAPACITY = -9        /* the input exceeds the fixed scratch size of
+    PTA_ECAPACITY = -9,       /* the input exceeds the fixed scratch size of
                                  pta_neighbours_noalloc                              */
+    PTA_ECHECK = -10          /* debug build only (compiled with PTA_CHECK=1): an atom,
+                                 cell or list index or a list count was out of its
+                                 range; the offending access was skipped and the
+                                 results are invalid                                 */
 } pta_status;
 
 enum { PTA_POT_SUTTON_CHEN_SF = 1 };

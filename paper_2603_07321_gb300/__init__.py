@@ -31,6 +31,7 @@ __all__ = [
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libpta.so")
+LIB_CHECK_PATH = os.path.join(_PKG, "_lib", "libpta_check.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -38,7 +39,7 @@ SRC_PREDICTED, SRC_MEASURE_JUMP, SRC_MEASURE_MISMATCH = 0, 1, 2
 
 _STATUS = {0: "PTA_OK", -1: "PTA_EINVAL", -2: "PTA_ENOMEM", -3: "PTA_ECUDA",
            -4: "PTA_ENEIGH_OVERFLOW", -5: "PTA_ENAN", -6: "PTA_ESTATE", -7: "PTA_ERANGE",
-           -8: "PTA_EUNSUPPORTED", -9: "PTA_ECAPACITY"}
+           -8: "PTA_EUNSUPPORTED", -9: "PTA_ECAPACITY", -10: "PTA_ECHECK"}
 
 
 class PTAError(RuntimeError):
@@ -169,18 +170,33 @@ _live = {}            # data_ptr -> torch tensor backing device memory handed to
 _callbacks = None
 
 
-def build(force: bool = False) -> str:
+def check_build() -> bool:
+    """True when this process uses the debug library (environment PTA_CHECK=1
+    when the library is first loaded): every index and count is tested on the
+    device, and a failed test gives PTA_ECHECK."""
+    return os.environ.get("PTA_CHECK", "0") == "1"
+
+
+def build(force: bool = False, check=None) -> str:
+    """Compile the library (the debug variant when check, by default when
+    check_build())."""
     from . import buildlib
-    return buildlib.build(force=force)
+    return buildlib.build(force=force, check=check_build() if check is None else bool(check))
 
 
-def load(path: str = LIB_PATH):
-    """Load libpta.so (built by build()); raises if it is missing."""
+def library_path() -> str:
+    return LIB_CHECK_PATH if check_build() else LIB_PATH
+
+
+def load(path: str = None):
+    """Load libpta.so (built by build()), or libpta_check.so when
+    check_build(); raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or library_path()
     if not os.path.exists(path):
-        raise ImportError("libpta.so not found at %s: run paper_2603_07321_gb300.build() "
+        raise ImportError("%s not found: run paper_2603_07321_gb300.build() "
                           "(there is no CPU fallback)" % path)
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():

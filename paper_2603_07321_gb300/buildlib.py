@@ -19,6 +19,9 @@ INC = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_lib")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libpta.so")
+# debug build: every index and count tested before use (-DPTA_CHECK=1)
+OBJ_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(OUT, "libpta_check.so")
 SOURCES = ["pta_api.cu", "k_setup.cu", "k_neigh.cu", "k_pair_f32.cu", "k_pair_f64.cu",
            "k_noalloc.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,22 +43,26 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile (what is stale of) the library; returns its path.  check=True
+    builds the debug variant libpta_check.so (PTA_CHECK=1) instead."""
+    obj_dir, lib = (OBJ_CHECK, LIB_CHECK) if check else (OBJ, LIB)
+    flags = FLAGS + (["-DPTA_CHECK=1"] if check else [])
     os.makedirs(OUT, exist_ok=True)
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INC, "pta.h"))
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, src + ".o")
+        o = os.path.join(obj_dir, src + ".o")
         if force or _stale(o, [s] + headers):
             jobs.append((s, o))
 
     def compile_one(job):
         s, o = job
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", s, "-o", o]
+        cmd = [nvcc] + ARCH + flags + ["-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (s, r.stderr))
@@ -66,16 +73,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(compile_one, jobs))
-    objs = [os.path.join(OBJ, src + ".o") for src in SOURCES]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    objs = [os.path.join(obj_dir, src + ".o") for src in SOURCES]
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s" % r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -133,6 +133,7 @@ __device__ __forceinline__ void atom_update_mixed(const SpecDev &S, SpecCtl *ctl
                                                   int phase, long long done, long long nsteps,
                                                   double &ke, double &pe, double &rr, float &d2,
                                                   float &dp2) {
+    chk_force(S, fx, fy, fz);
     const float eps = S.pot.f_eps;
     const float pe_a = 0.5f * eps * en + (fpa != 0.f ? S.pot.f_ec2hq / fpa : 0.f);
     pe += (double)pe_a;

@@ -83,7 +83,7 @@ __global__ void k_scatter(const SpecDev *__restrict__ specs, const int *__restri
     const int a = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
     if (a >= S.n) return;
     const int c = S.atom_cell[a];
-    const int slot = S.cell_start[c] + atomicAdd(&S.cell_cnt[c], 1);
+    const int slot = chk_index(S, S.cell_start[c] + atomicAdd(&S.cell_cnt[c], 1), S.n);
     S.cell_tmp[slot] = a;
 }
 
@@ -103,11 +103,11 @@ __global__ void k_cell_sort(const SpecDev *__restrict__ specs, const int *__rest
         if (c >= S.ncell) return;
         const int s = S.cell_start[c], e = S.cell_start[c + 1];
         for (int p = s + lane; p < e; p += 32) {
-            const int v = S.cell_tmp[p];
+            const int v = chk_index(S, S.cell_tmp[chk_index(S, p, S.n)], S.n);
             const int ov = S.orig[v];
             int r = 0;
-            for (int q = s; q < e; ++q) r += (S.orig[S.cell_tmp[q]] < ov);
-            S.cell_atoms[s + r] = v;
+            for (int q = s; q < e; ++q) r += (S.orig[chk_index(S, S.cell_tmp[chk_index(S, q, S.n)], S.n)] < ov);
+            S.cell_atoms[chk_index(S, s + r, S.n)] = v;
         }
         if (lane == 0) S.cell_cnt[c] = 0;
     }
@@ -120,7 +120,7 @@ __global__ void k_permute_gather(const SpecDev *__restrict__ specs, const int *_
     if (!build_active(S, force)) return;
     const int p = (blockIdx.x - S.blk_atom0) * TPB + threadIdx.x;
     if (p >= S.n) return;
-    const int src = S.cell_atoms[p];
+    const int src = chk_index(S, S.cell_atoms[p], S.n);
     const int par = S.ctl->parity;
     const PermLayout Lo = perm_layout(S.n, S.prec);
     char *t = (char *)S.perm_tmp;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                                         yy < S.nc[1] && zz < S.nc[2];
                     if (inside) {
                         const int cc = cell_rank(S.nc, xx, yy, zz);
-                        const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
+                        const int s = chk_count(S, S.cell_start[cc], S.n), e = chk_count(S, S.cell_start[cc + 1], S.n);
                         // half-cell offset 2d + sub_j - sub_a: add the spread bits of j
                         const unsigned code = nl_entry(0, 2 * dx, 2 * dy, 2 * dz) - (unsigned)own_sub;
                         // position of atom a relative to the centre of cell cc
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
             for (int yy = max(cy - 1, 0); yy <= min(cy + 1, S.nc[1] - 1); ++yy)
                 for (int xx = max(cx - 1, 0); xx <= min(cx + 1, S.nc[0] - 1); ++xx) {
                     const int cc = cell_rank(S.nc, xx, yy, zz);
-                    const int s = S.cell_start[cc], e = S.cell_start[cc + 1];
+                    const int s = chk_count(S, S.cell_start[cc], S.n), e = chk_count(S, S.cell_start[cc + 1], S.n);
                     const unsigned code =
                         mixed ? nl_entry(0, 2 * (xx - cx), 2 * (yy - cy), 2 * (zz - cz)) -
                                     (unsigned)sub0

@@ -33,11 +33,11 @@ namespace pta {
 __device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, int l, int L, int &cl) {
     const long long off = nl_base(u, L, S.cap) + l;
     if (S.prune_on) {
-        cl = S.pnn[(long long)u * L + l];
+        cl = chk_count(S, S.pnn[(long long)u * L + l], S.cap_use / L);
         return (const unsigned *)S.plist + off;
     }
     const int nn = S.nn[u];
-    cl = nn > l ? (nn - l + L - 1) / L : 0;
+    cl = chk_count(S, nn > l ? (nn - l + L - 1) / L : 0, S.cap_use / L);
     return (const unsigned *)S.nlist + off;
 }
 
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             for (int q = 0; q < cl; q += 4) {
                 const unsigned n0 = ld_list(lst + (q + 4) * 32), n1 = ld_list(lst + (q + 5) * 32);
                 const unsigned n2 = ld_list(lst + (q + 6) * 32), n3 = ld_list(lst + (q + 7) * 32);
-                const float4 x0 = __ldg(rel + nl_j(e0)), x1 = __ldg(rel + nl_j(e1));
-                const float4 x2 = __ldg(rel + nl_j(e2)), x3 = __ldg(rel + nl_j(e3));
+                const float4 x0 = __ldg(rel + nl_atom(S, e0)), x1 = __ldg(rel + nl_atom(S, e1));
+                const float4 x2 = __ldg(rel + nl_atom(S, e2)), x3 = __ldg(rel + nl_atom(S, e3));
                 float2 dx, dy, dz;
                 entry_disp2(e0, e1, x0, x1, ra, h, h8, h64, dx, dy, dz);
                 rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
             unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
             for (int q = 0; q < cl; q += 2) {
                 const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
-                const float4 xa = __ldg(rel + nl_j(ea));
-                const float4 xb = __ldg(rel + nl_j(eb));
+                const float4 xa = __ldg(rel + nl_atom(S, ea));
+                const float4 xb = __ldg(rel + nl_atom(S, eb));
                 float2 dx, dy, dz;
                 entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
                 rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             for (int q = 0; q < cl; q += 4) {
                 const unsigned n0 = ld_list(lst + (q + 4) * 32), n1 = ld_list(lst + (q + 5) * 32);
                 const unsigned n2 = ld_list(lst + (q + 6) * 32), n3 = ld_list(lst + (q + 7) * 32);
-                const float4 x0 = __ldg(lf + nl_j(e0)), x1 = __ldg(lf + nl_j(e1));
-                const float4 x2 = __ldg(lf + nl_j(e2)), x3 = __ldg(lf + nl_j(e3));
+                const float4 x0 = __ldg(lf + nl_atom(S, e0)), x1 = __ldg(lf + nl_atom(S, e1));
+                const float4 x2 = __ldg(lf + nl_atom(S, e2)), x3 = __ldg(lf + nl_atom(S, e3));
                 two(e0, e1, x0, x1, true, q + 1 < cl);
                 if (q + 2 < cl) two(e2, e3, x2, x3, true, q + 3 < cl);
                 e0 = n0; e1 = n1; e2 = n2; e3 = n3;
@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
             unsigned ea = ld_list(lst), eb = ld_list(lst + 32);
             for (int q = 0; q < cl; q += 2) {
                 const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
-                const float4 xa = __ldg(lf + nl_j(ea));
-                const float4 xb = __ldg(lf + nl_j(eb));
+                const float4 xa = __ldg(lf + nl_atom(S, ea));
+                const float4 xb = __ldg(lf + nl_atom(S, eb));
                 two(ea, eb, xa, xb, true, q + 1 < cl);
                 ea = na;
                 eb = nb;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(TPB, 7) k_prune_f32(const SpecDev *__restrict_
     const unsigned *__restrict__ src = (const unsigned *)S.nlist + off;
     unsigned *__restrict__ dst = (unsigned *)S.plist + off;
     const int nn = S.nn[u];
-    const int cl = nn > l ? (nn - l + L - 1) / L : 0;
+    const int cl = chk_count(S, nn > l ? (nn - l + L - 1) / L : 0, S.cap_use / L);
     int kept = 0;
     // eight entries per iteration (eight gathers in flight), the next eight
     // words read ahead: rows up to cl + 14, within the spare iterations
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(TPB, 7) k_prune_f32(const SpecDev *__restrict_
         for (int k = 0; k < 8; ++k) nx[k] = ld_list(src + (q + 8 + k) * 32);
         float4 x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = __ldg(rel + nl_j(e[k]));
+        for (int k = 0; k < 8; ++k) x[k] = __ldg(rel + nl_atom(S, e[k]));
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
             float2 dx, dy, dz;

@@ -29,10 +29,10 @@ __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__
     double4_32a pa = make_double4_32a(0, 0, 0, 0);
     if (valid) {
         pa = pos[a];
-        const int nn = S.nn[a];
+        const int nn = chk_count(S, S.nn[a], S.cap_use);
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
         for (int k = l; k < nn; k += L) {
-            const int j = nl_j((unsigned)lst[(k / L) * 32 + (k % L)]);
+            const int j = nl_atom(S, (unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pos[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r = sqrt((dx * dx + dy * dy) + dz * dz);
@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
     double4_32a pa = make_double4_32a(0, 0, 0, 0);
     if (valid) {
         pa = pf[a];
-        const int nn = S.nn[a];
+        const int nn = chk_count(S, S.nn[a], S.cap_use);
         const int *__restrict__ lst = S.nlist + nl_base(a, L, S.cap);
         for (int k = l; k < nn; k += L) {
-            const int j = nl_j((unsigned)lst[(k / L) * 32 + (k % L)]);
+            const int j = nl_atom(S, (unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pf[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r = sqrt((dx * dx + dy * dy) + dz * dz);
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
     en = lane_sum<L>(en);
     double ke = 0, pe = 0, rr = 0, d2 = 0;
     if (valid && l == 0) {
+        chk_force(S, fx, fy, fz);
         const double fpa = pa.w;
         // B(rho) = -eps c sqrt(rho) = (eps c)^2 / (2 B'(rho))
         pe = 0.5 * P.eps * en + (fpa != 0.0 ? 0.5 * P.ec * P.ec / fpa : 0.0);

@@ -435,7 +435,8 @@ __global__ void k_burst_end(const SpecDev *__restrict__ specs, int slot, pta_ave
         r.converged = adaptive ? c->conv_mask : 0;
         for (int q = 0; q < 3; ++q) r.nsamples[q] = nq[q];
         int e = c->err;
-        r.status = (e & ERR_OVERFLOW) ? PTA_ENEIGH_OVERFLOW
+        r.status = (e & ERR_CHECK)    ? PTA_ECHECK
+                   : (e & ERR_OVERFLOW) ? PTA_ENEIGH_OVERFLOW
                    : (e & ERR_NAN)    ? PTA_ENAN
                    : (e & (ERR_RANGE | ERR_GRID)) ? PTA_ERANGE
                                       : PTA_OK;

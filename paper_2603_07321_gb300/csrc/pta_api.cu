@@ -1433,7 +1433,11 @@ int pta_forces(pta_ctx *c, double *f, double *pe, int64_t n, double obs[3]) {
     }
     if (obs)
         for (int q = 0; q < 3; ++q) obs[q] = ctl.eval_obs[q];
+    if (ctl.err & ERR_CHECK) return PTA_ECHECK;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
+#if PTA_CHECK
+    if (ctl.err & ERR_NAN) return PTA_ENAN;  // the debug build's force scan
+#endif
     if (ctl.err & ERR_GRID) return PTA_ERANGE;
     return PTA_OK;
 }
@@ -1459,6 +1463,7 @@ int pta_get_neighbours(pta_ctx *c, int32_t *counts, int32_t *list, int64_t n, in
     CKR(fetch_orig(c, orig));
     CK(cudaStreamSynchronize(c->stream));
     *max_count = ctl.max_nn;
+    if (ctl.err & ERR_CHECK) return PTA_ECHECK;
     if (ctl.err & ERR_OVERFLOW) return PTA_ENEIGH_OVERFLOW;
     int maxc = 0;
     for (int64_t u = 0; u < n; ++u) {

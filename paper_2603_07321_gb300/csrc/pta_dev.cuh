@@ -28,8 +28,19 @@ constexpr double MIXED_RANGE = 511.0;
 
 enum Phase : int { PH_IDLE = 0, PH_REFRESH = 1, PH_RUN = 2 };
 // ERR_GRID: an atom lay beyond the cell grid's margin at a list build (it is
-// binned onto the nearest border cell, which keeps the pair search complete)
-enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4, ERR_GRID = 8 };
+// binned onto the nearest border cell, which keeps the pair search complete);
+// ERR_CHECK: a debug build's index or count test failed
+enum ErrBit : int { ERR_OVERFLOW = 1, ERR_NAN = 2, ERR_RANGE = 4, ERR_GRID = 8, ERR_CHECK = 16 };
+
+// Debug builds (compiled with -DPTA_CHECK=1) test every atom, cell-slot and
+// list index before the access it feeds, every list count against the
+// list's capacity, the cell occupancy against the atom count, and every
+// atom's force for finiteness; a failed test sets ERR_CHECK (ERR_NAN for a
+// force) and the access goes to index 0 instead, so a debug build never
+// reads or writes out of bounds.  Production builds compile the tests away.
+#ifndef PTA_CHECK
+#define PTA_CHECK 0
+#endif
 // mixed precision: velocity as an exact FP32 pair v = h + l
 struct __align__(32) VelHL {
     float4 h, l;
@@ -191,6 +202,39 @@ __host__ __device__ __forceinline__ unsigned nl_entry(int j, int dx, int dy, int
     return ((unsigned)j << NL_CODE_BITS) | (unsigned)((dx + 3) | ((dy + 3) << 3) | ((dz + 3) << 6));
 }
 __host__ __device__ __forceinline__ int nl_j(unsigned e) { return (int)(e >> NL_CODE_BITS); }
+
+// index i of an array of n elements (debug builds: tested, 0 when outside)
+__device__ __forceinline__ int chk_index(const SpecDev &S, int i, int n) {
+#if PTA_CHECK
+    if ((unsigned)i >= (unsigned)n) {
+        atomicOr(&S.ctl->err, ERR_CHECK);
+        return 0;
+    }
+#endif
+    return i;
+}
+
+// the atom a list entry names
+__device__ __forceinline__ int nl_atom(const SpecDev &S, unsigned e) { return chk_index(S, nl_j(e), S.n); }
+
+// a count of list entries read by one lane (debug builds: at most `limit`)
+__device__ __forceinline__ int chk_count(const SpecDev &S, int c, int limit) {
+#if PTA_CHECK
+    if (c < 0 || c > limit) {
+        atomicOr(&S.ctl->err, ERR_CHECK);
+        return c < 0 ? 0 : limit;
+    }
+#endif
+    return c;
+}
+
+// an atom's force (debug builds: finite)
+__device__ __forceinline__ void chk_force(const SpecDev &S, double fx, double fy, double fz) {
+#if PTA_CHECK
+    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&S.ctl->err, ERR_NAN);
+#endif
+    (void)S; (void)fx; (void)fy; (void)fz;
+}
 
 // The three offsets as exact FP32 multiples of the axis field, without
 // integer conversion: OR-ing a field into the mantissa of 1.5 * 2^23
@@ -359,6 +403,9 @@ __device__ __forceinline__ void scan_cells(const SpecDev &S) {
     if (threadIdx.x == 0) {
         S.cell_start[S.ncell] = carry;
         S.ctl->rebuilds += 1;
+#if PTA_CHECK
+        if (carry != S.n) atomicOr(&S.ctl->err, ERR_CHECK);  // every atom in one cell
+#endif
     }
 }
 
