@@ -15,6 +15,7 @@ the library or the GPU is missing.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 
 import numpy as np
@@ -512,16 +513,25 @@ def pta_neighbours_noalloc(pos_dev_ptr: int, n: int, box_lo, box_hi, rlist: floa
 # ---------------------------------------------------------------------------
 # handle wrappers
 # ---------------------------------------------------------------------------
+_TAGS = itertools.count()
+
+
 class Ctx:
     """One specimen on the device (owns a pta_ctx)."""
 
     def __init__(self, n_cells, T0=300.0, seed=1, params: Params | None = None,
                  potential: Potential | None = None, load_axis=2, a0=4.05, grip_width=0.0,
-                 stream=None, tuned: bool = True, replicas: int = 1, **param_kw):
+                 stream=None, tuned: bool = True, replicas: int = 1, log=None, tag=None,
+                 **param_kw):
         """With the threads per atom left automatic (no params, lanes 0 or
         absent) and `tuned`, the layout the autotuner cached for this size,
         precision and number of replicas sharing the device (tune.py) is
-        used; without a cache entry the library's own choice."""
+        used; without a cache entry the library's own choice.  With `log` (a
+        metrics.JsonlLog, a path or a text file) every burst, relaxation and
+        coarse step appends a record named by `tag`."""
+        from . import metrics as _metrics
+        self.log = _metrics.as_log(log)
+        self.tag = tag if tag is not None else "ctx%d" % next(_TAGS)
         self.spec = make_specimen(n_cells, a0, load_axis, grip_width)
         self.layout_source = "explicit" if (params is not None or param_kw.get("lanes")) \
             else "automatic"
@@ -558,8 +568,14 @@ class Ctx:
     def mean_positions(self):
         return pta_get_mean_positions(self.h, self.n)
 
+    def _log(self, kind, **fields):
+        if self.log is not None:
+            self.log.write(kind, tag=self.tag, **fields)
+
     def relax(self, window=2000, max_steps=50000, tol_gpa=0.05):
-        return pta_relax(self.h, window, max_steps, tol_gpa)
+        a, steps = pta_relax(self.h, window, max_steps, tol_gpa)
+        self._log("relax", steps=steps, window=a.as_dict())
+        return a, steps
 
     def apply_strain(self, d_eps):
         pta_apply_strain(self.h, d_eps)
@@ -569,16 +585,22 @@ class Ctx:
         return pta_get_strain(self.h)
 
     def fine_burst(self, nsteps):
-        return pta_fine_burst(self.h, nsteps)
+        a = pta_fine_burst(self.h, nsteps)
+        self._log("burst", **a.as_dict())
+        return a
 
     def ramp_burst(self, nsteps, d_eps_per_step):
-        return pta_ramp_burst(self.h, nsteps, d_eps_per_step)
+        a = pta_ramp_burst(self.h, nsteps, d_eps_per_step)
+        self._log("ramp_burst", d_eps_per_step=d_eps_per_step, **a.as_dict())
+        return a
 
     def series(self, max_steps=1 << 20):
         return pta_get_series(self.h, max_steps)
 
     def coarse_step(self):
-        return pta_coarse_step(self.h)
+        r = pta_coarse_step(self.h)
+        self._log("coarse", **r.as_dict())
+        return r
 
     def coarse_update(self, means):
         return pta_coarse_update(self.h, means)
@@ -629,16 +651,21 @@ class Batch:
     def apply_strain(self, d_eps):
         pta_batch_apply_strain(self.h, d_eps)
 
+    def _log(self, kind, results):
+        for m, r in zip(self.members, results):
+            m._log(kind, **r.as_dict())
+        return results
+
     def fine_burst(self, nsteps):
         if np.isscalar(nsteps):
             nsteps = [nsteps] * len(self.members)
-        return pta_batch_fine_burst(self.h, nsteps)
+        return self._log("burst", pta_batch_fine_burst(self.h, nsteps))
 
     def coarse_step(self):
-        return pta_batch_coarse_step(self.h, len(self.members))
+        return self._log("coarse", pta_batch_coarse_step(self.h, len(self.members)))
 
     def tick(self):
-        return pta_batch_tick(self.h, len(self.members))
+        return self._log("coarse", pta_batch_tick(self.h, len(self.members)))
 
     def set_timing(self, enable=True):
         pta_batch_set_timing(self.h, enable)

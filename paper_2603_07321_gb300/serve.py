@@ -56,7 +56,11 @@ class SchedulerError(RuntimeError):
 class Scheduler:
     """Admission by slots and device-memory footprint, FIFO order."""
 
-    def __init__(self, engine, mem_budget_bytes: int, max_slots: int = 64, clock=None):
+    def __init__(self, engine, mem_budget_bytes: int, max_slots: int = 64, clock=None, log=None):
+        """log: a metrics.JsonlLog (or a path / text file) receiving one record
+        per request event, per tick and per specimen coarse step."""
+        from .metrics import as_log
+        self.log = as_log(log)
         self.engine = engine
         self.budget = int(mem_budget_bytes)
         self.max_slots = int(max_slots)
@@ -74,16 +78,21 @@ class Scheduler:
             self.t0 = self.clock()
         return self.clock() - self.t0
 
+    def _event(self, kind, **fields):
+        if self.log is not None:
+            self.log.write(kind, **fields)
+
     def submit(self, req: Request):
         err = self.engine.validate(req)
+        if not err and self.engine.footprint(req) > self.budget:
+            err = "larger than the memory budget"
         if err:
             self.results[req.rid] = Result(req.rid, "rejected", req.arrival_s, error=err)
-            return False
-        if self.engine.footprint(req) > self.budget:
-            self.results[req.rid] = Result(req.rid, "rejected", req.arrival_s,
-                                           error="larger than the memory budget")
+            self._event("request_rejected", tag=req.rid, error=err)
             return False
         self.waiting.append(req)
+        self._event("request_queued", tag=req.rid, arrival_s=req.arrival_s, n_cells=req.n_cells,
+                    T0=req.T0, strain_rate=req.strain_rate, target_strain=req.target_strain)
         return True
 
     # ------------------------------------------------------------- admission
@@ -103,12 +112,14 @@ class Scheduler:
             except Exception as e:             # invalid on the device: reject
                 self.waiting.pop(0)
                 self.results[req.rid] = Result(req.rid, "rejected", req.arrival_s, error=str(e))
+                self._event("request_rejected", tag=req.rid, error=str(e))
                 continue
             self.waiting.pop(0)
             res = Result(req.rid, "running", req.arrival_s, admitted_s=now)
             self.live[req.rid] = {"req": req, "handle": h, "bytes": need, "result": res}
             self.used += need
             admitted.append(req.rid)
+            self._event("request_admitted", tag=req.rid, wait_s=now - req.arrival_s, bytes=need)
         return admitted
 
     def _retire(self, rid: int, status: str, now: float, error: str = ""):
@@ -120,6 +131,8 @@ class Scheduler:
         res.finished_s = now
         res.error = error
         self.results[rid] = res
+        self._event("request_" + status, tag=rid, curve_latency_s=now - res.arrival_s,
+                    coarse_steps=len(res.curve), atom_steps=res.atom_steps, error=error)
 
     # ------------------------------------------------------------------ loop
     def tick(self) -> bool:
@@ -136,6 +149,7 @@ class Scheduler:
         dt = self.clock() - t
         now = self.now()
         self.ticks += 1
+        self._event("tick", live=len(rids), latency_s=dt)
         for rid, out in zip(rids, outs):
             slot = self.live[rid]
             res = slot["result"]
@@ -146,6 +160,8 @@ class Scheduler:
             res.atom_steps += out["atom_steps"]
             if not out.get("initial"):
                 res.curve.append((out["strain"], out["v"], out["source"]))
+            self._event("coarse", tag=rid, initial=bool(out.get("initial")),
+                        strain=out["strain"], v=list(out["v"]), source=list(out["source"]))
             req = slot["req"]
             if abs(out["strain"]) >= req.target_strain - 1e-12:
                 self._retire(rid, "done", now)
