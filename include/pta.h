@@ -64,7 +64,7 @@ typedef enum {
                                  representation holds (|x| < 512 A), an atom left
                                  the cell grid (its margin of a quarter of the
                                  specimen's extent around the lattice), or a
-                                 specimen has more than 2^23 atoms                   */
+                                 specimen has 2^23 or more atoms                     */
     PTA_EUNSUPPORTED = -8,    /* an option this build does not provide                 */
     PTA_ECAPACITY = -9,       /* the input exceeds the fixed scratch size of
                                  pta_neighbours_noalloc                              */

@@ -305,9 +305,11 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
         const int top = __reduce_max_sync(0xffffffffu, valid ? min(cnt, S.cap_use) : 0);
         if (wvalid) wr.flush(top);
         if (valid) {
-            // the row after the last entry is read (and gathered) by the
-            // unrolled pair loops: a filler entry
-            wr.tile[(long long)min(cnt, S.cap_use) * 32 + lane] = 0;
+            // four sentinel rows after the last entry: the pair loops read
+            // the list in groups of four (within the sixteen spare rows)
+            const unsigned sen = nl_sentinel(S.n);
+            const int c0 = min(cnt, S.cap_use);
+            for (int r = 0; r < 4; ++r) wr.tile[(long long)(c0 + r) * 32 + lane] = (int)sen;
             S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
             S.ref[a] = make_float4((float)xa, (float)ya, (float)za, 0.f);
         }
@@ -375,7 +377,15 @@ __global__ void __launch_bounds__(TPB) k_build(const SpecDev *__restrict__ specs
                         }
                     }
                 }
-        S.nn[u] = cnt < S.cap_use ? cnt : S.cap_use;
+        const int c0 = cnt < S.cap_use ? cnt : S.cap_use;
+        if (mixed) {
+            // four sentinel entries per lane after the last entry (the pair
+            // loops read each lane's column in groups of four)
+            const unsigned sen = nl_sentinel(S.n);
+            for (int k = c0; k < c0 + 4 * L; ++k)
+                S.nlist[base + (long long)(k / L) * 32 + (k % L)] = (int)sen;
+        }
+        S.nn[u] = c0;
         S.ref[a] = make_float4((float)x, (float)y, (float)z, 0.f);
     }
     // block maximum of the counts, one atomic per block

@@ -23,21 +23,26 @@
 
 namespace pta {
 
-// The entry loop is unrolled by two (by four in the density pass); the next
-// two (four) entries are read before the current ones are evaluated.  Those
-// reads go past an atom's count into the sixteen spare iterations every list
-// keeps, whose entries are valid indices, so the loop carries no bounds tests.
+// Every lane's list ends with sentinel entries that bring its count to a
+// multiple of four (they name a record far from every atom, so their pairs
+// fail the cutoff test like any distant neighbour): the loops take four
+// entries per iteration (two with several lanes per atom) without per-entry
+// bounds tests, and read the next group's list words before evaluating the
+// current one; those reads go past the count into the sixteen spare rows
+// every list keeps and are never gathered.
 
 // the entries lane l of atom u reads (the inner list when pruning is on, else
-// the Verlet list), as a pointer to its first word (stride 32) and a count
+// the Verlet list), as a pointer to its first word (stride 32) and a count,
+// rounded up to a multiple of four over the sentinel rows
 __device__ __forceinline__ const unsigned *lane_list(const SpecDev &S, int u, int l, int L, int &cl) {
     const long long off = nl_base(u, L, S.cap) + l;
     if (S.prune_on) {
-        cl = chk_count(S, S.pnn[(long long)u * L + l], S.cap_use / L);
+        cl = chk_count(S, S.pnn[(long long)u * L + l], S.cap_use / L + 4);
         return (const unsigned *)S.plist + off;
     }
     const int nn = S.nn[u];
-    cl = chk_count(S, nn > l ? (nn - l + L - 1) / L : 0, S.cap_use / L);
+    cl = chk_count(S, (nn > l ? (nn - l + L - 1) / L : 0), S.cap_use / L);
+    cl = (cl + 3) & ~3;
     return (const unsigned *)S.nlist + off;
 }
 
@@ -68,9 +73,9 @@ __device__ __forceinline__ void entry_disp2(unsigned ea, unsigned eb, float4 xa,
     dz = __ffma2_rn(oz, f2(h64), __fadd2_rn(make_float2(xa.z, xb.z), f2(-r0.z)));
 }
 
-// density terms of two entries (b only when vb), added in entry order
+// density terms of two entries, added in entry order
 template <bool SC76>
-__device__ __forceinline__ void rho_add2(const PotF &P, float2 dx, float2 dy, float2 dz, bool vb,
+__device__ __forceinline__ void rho_add2(const PotF &P, float2 dx, float2 dy, float2 dz,
                                          float &rho) {
     float2 r2 = __fmul2_rn(dx, dx);
     r2 = __ffma2_rn(dy, dy, r2);
@@ -79,10 +84,10 @@ __device__ __forceinline__ void rho_add2(const PotF &P, float2 dx, float2 dy, fl
     if (SC76) {
         const float2 phi = phi_m2_sc76(P, r2);
         if (r2.x < rc2) rho += phi.x;
-        if (vb && r2.y < rc2) rho += phi.y;
+        if (r2.y < rc2) rho += phi.y;
     } else {
         if (r2.x < rc2) rho += phi_m1<false>(P, r2.x);
-        if (vb && r2.y < rc2) rho += phi_m1<false>(P, r2.y);
+        if (r2.y < rc2) rho += phi_m1<false>(P, r2.y);
     }
 }
 
@@ -115,11 +120,9 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
                 const float4 x2 = __ldg(rel + nl_atom(S, e2)), x3 = __ldg(rel + nl_atom(S, e3));
                 float2 dx, dy, dz;
                 entry_disp2(e0, e1, x0, x1, ra, h, h8, h64, dx, dy, dz);
-                rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
-                if (q + 2 < cl) {
-                    entry_disp2(e2, e3, x2, x3, ra, h, h8, h64, dx, dy, dz);
-                    rho_add2<SC76>(P, dx, dy, dz, q + 3 < cl, rho);
-                }
+                rho_add2<SC76>(P, dx, dy, dz, rho);
+                entry_disp2(e2, e3, x2, x3, ra, h, h8, h64, dx, dy, dz);
+                rho_add2<SC76>(P, dx, dy, dz, rho);
                 e0 = n0; e1 = n1; e2 = n2; e3 = n3;
             }
         } else {
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(TPB, 8) k_density_f32(const SpecDev *__restric
                 const float4 xb = __ldg(rel + nl_atom(S, eb));
                 float2 dx, dy, dz;
                 entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
-                rho_add2<SC76>(P, dx, dy, dz, q + 1 < cl, rho);
+                rho_add2<SC76>(P, dx, dy, dz, rho);
                 ea = na;
                 eb = nb;
             }
@@ -170,14 +173,14 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
         const unsigned *__restrict__ lst = lane_list(S, u, l, L, cl);
         // the offsets of two entries decoded in packed instructions; the pair
         // terms stay scalar (packed, they measured slower here)
-        auto two = [&](unsigned ea, unsigned eb, float4 xa, float4 xb, bool va, bool vb) {
+        auto two = [&](unsigned ea, unsigned eb, float4 xa, float4 xb) {
             float2 dx, dy, dz;
             entry_disp2(ea, eb, xa, xb, ra, h, h8, h64, dx, dy, dz);
             const float r2a = dx.x * dx.x + dy.x * dy.x + dz.x * dz.x;
-            if (va && r2a < rc2)
+            if (r2a < rc2)
                 force_pair<SC76>(P, dx.x, dy.x, dz.x, r2a, ra.w + xa.w, fx, fy, fz, e7, er);
             const float r2b = dx.y * dx.y + dy.y * dy.y + dz.y * dz.y;
-            if (vb && r2b < rc2)
+            if (r2b < rc2)
                 force_pair<SC76>(P, dx.y, dy.y, dz.y, r2b, ra.w + xb.w, fx, fy, fz, e7, er);
         };
         if constexpr (L == 1) {
@@ -188,8 +191,8 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
                 const unsigned n2 = ld_list(lst + (q + 6) * 32), n3 = ld_list(lst + (q + 7) * 32);
                 const float4 x0 = __ldg(lf + nl_atom(S, e0)), x1 = __ldg(lf + nl_atom(S, e1));
                 const float4 x2 = __ldg(lf + nl_atom(S, e2)), x3 = __ldg(lf + nl_atom(S, e3));
-                two(e0, e1, x0, x1, true, q + 1 < cl);
-                if (q + 2 < cl) two(e2, e3, x2, x3, true, q + 3 < cl);
+                two(e0, e1, x0, x1);
+                two(e2, e3, x2, x3);
                 e0 = n0; e1 = n1; e2 = n2; e3 = n3;
             }
         } else {
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
                 const unsigned na = ld_list(lst + (q + 2) * 32), nb = ld_list(lst + (q + 3) * 32);
                 const float4 xa = __ldg(lf + nl_atom(S, ea));
                 const float4 xb = __ldg(lf + nl_atom(S, eb));
-                two(ea, eb, xa, xb, true, q + 1 < cl);
+                two(ea, eb, xa, xb);
                 ea = na;
                 eb = nb;
             }
@@ -225,7 +228,8 @@ __global__ void __launch_bounds__(TPB, 8) k_force_f32(const SpecDev *__restrict_
 // Inner list: every lane keeps, in order, the entries of its own column of
 // the Verlet list that lie within the pruning radius of the atom (FP32
 // distances tested against (rc + margin)^2 widened by 1e-5).  Pairs within
-// rc are therefore all kept, in the order the lane sums them.
+// rc are therefore all kept, in the order the lane sums them.  Sentinel
+// entries then bring the lane's count to a multiple of four.
 template <int L>
 __global__ void __launch_bounds__(TPB, 7) k_prune_f32(const SpecDev *__restrict__ specs,
                                                       const int *__restrict__ b2s, int force) {
@@ -268,6 +272,10 @@ __global__ void __launch_bounds__(TPB, 7) k_prune_f32(const SpecDev *__restrict_
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) e[k] = nx[k];
+    }
+    {
+        const unsigned sen = nl_sentinel(S.n);
+        while (kept & 3) dst[(kept++) * 32] = sen;
     }
     S.pnn[(long long)u * L + l] = kept;
     if (l == 0) {

@@ -312,10 +312,10 @@ static int compute_sizes(const pta_specimen &s, const pta_potential &p, const pt
         const double nb = 4.0 / 3.0 * 3.141592653589793 * rl * rl * rl * dens;
         z->cap_use = (int)round_up((size_t)std::ceil(1.6 * nb + 16), 32);
     }
-    // sixteen spare iterations per atom: the pair loops read up to eight
-    // entries ahead and the pruning up to fifteen, without bounds tests
-    // (spare entries hold earlier, valid
-    // indices or 0)
+    // sixteen spare rows per lane: they hold the (up to four) sentinel rows
+    // after a full list, the pair loops read four rows ahead and the pruning
+    // fifteen, without bounds tests (spare entries hold 0, earlier entries or
+    // the sentinel: all valid record indices)
     z->cap = z->cap_use + 16 * z->L;
     z->nblk_pair = (int)((z->n * z->L + TPB - 1) / TPB);
     z->nblk_atom = (int)((z->n + TPB - 1) / TPB);
@@ -355,11 +355,11 @@ static size_t footprint(const Sizes &z, int prec) {
     if (prec != PTA_PREC_FP64) {
         add(16 * n);
         add(16 * n);                 // lo[2]
-        add(16 * n);
-        add(16 * n);                 // rel[2]
+        add(16 * (n + 1));
+        add(16 * (n + 1));           // rel[2], + the sentinel record
         add(n);                      // hsub
     }
-    add(p * n);                      // posfp
+    add(p * (n + 1));                // posfp, + the sentinel record
     add(32 * n);                     // vel (double4 or hi/lo FP32)
     add(n);                          // flags
     add(16 * n);                     // ref
@@ -413,7 +413,7 @@ static int validate(const pta_specimen *s, const pta_potential *p, const pta_par
     for (int q = 0; q < 3; ++q)
         if (!(par->conv_tol[q] >= 0) || !std::isfinite(par->conv_tol[q])) return PTA_EINVAL;
     const long long n = 4LL * s->n_cells[0] * s->n_cells[1] * s->n_cells[2];
-    if (n > (long long)MAX_ATOMS) return PTA_ERANGE;
+    if (n >= (long long)MAX_ATOMS) return PTA_ERANGE;  // slot n is the lists' sentinel
     if (par->precision == PTA_PREC_MIXED) {
         for (int d = 0; d < 3; ++d)
             if (s->n_cells[d] * s->a0 * 1.5 > MIXED_RANGE) return PTA_ERANGE;
@@ -1021,11 +1021,11 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
     if (!f64) {
         AL(lo[0], 16 * n, float4 *);
         AL(lo[1], 16 * n, float4 *);
-        AL(rel[0], 16 * n, float4 *);
-        AL(rel[1], 16 * n, float4 *);
+        AL(rel[0], 16 * (n + 1), float4 *);
+        AL(rel[1], 16 * (n + 1), float4 *);
         AL(hsub, n, uint8_t *);
     }
-    AL(posfp, p * n, void *);
+    AL(posfp, p * (n + 1), void *);
     AL(vel, 32 * n, void *);
     AL(flags, n, uint8_t *);
     AL(ref, 16 * n, float4 *);
@@ -1151,6 +1151,18 @@ int pta_create(const pta_specimen *spec, const pta_potential *pot, double T0, ui
         if (cudaMemcpyAsync(c->d_self, &c->hd, sizeof(SpecDev), cudaMemcpyHostToDevice,
                             c->stream) != cudaSuccess)
             rc = PTA_ECUDA;
+    }
+    if (rc == PTA_OK && c->par.precision != PTA_PREC_FP64) {
+        // the sentinel record (slot n) that pads every lane's list to a
+        // multiple of four entries: far from every atom in both record
+        // buffers and in the force pass's records, never written again
+        static const float4 far_rec = {SENTINEL_COORD, SENTINEL_COORD, SENTINEL_COORD, 0.f};
+        const size_t n = (size_t)s.n;
+        float4 *dst[3] = {s.rel[0] + n, s.rel[1] + n, (float4 *)s.posfp + n};
+        for (float4 *d : dst)
+            if (cudaMemcpyAsync(d, &far_rec, sizeof(float4), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess)
+                rc = PTA_ECUDA;
     }
     if (rc == PTA_OK) {
         const double kT = kb_ev() * T0;

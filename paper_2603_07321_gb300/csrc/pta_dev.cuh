@@ -195,13 +195,22 @@ struct Tab {
 // 3x3x3 cells around a cell, |d| <= 3); with half-cell centres and h on
 // exact grids, r_j - r_i = (rel_j - rel_i) + (h / 2) d.  FP64 lists keep
 // whole-cell offsets, which its kernels do not read.
+//
+// Mixed-precision lists end, in every lane, with up to three sentinel
+// entries that bring the lane's count to a multiple of four: they name slot
+// n, a record kept far from every atom (SENTINEL_COORD on each axis), whose
+// pairs lie beyond any cutoff, so the pair loops take four entries at a time
+// without per-entry bounds tests.  Slot n must fit the index field: n < 2^23.
 constexpr int NL_CODE_BITS = 9;
 constexpr int MAX_ATOMS = 1 << 23;
+constexpr float SENTINEL_COORD = 1.0e4f;
 
 __host__ __device__ __forceinline__ unsigned nl_entry(int j, int dx, int dy, int dz) {
     return ((unsigned)j << NL_CODE_BITS) | (unsigned)((dx + 3) | ((dy + 3) << 3) | ((dz + 3) << 6));
 }
 __host__ __device__ __forceinline__ int nl_j(unsigned e) { return (int)(e >> NL_CODE_BITS); }
+// the sentinel entry of a specimen of n atoms (slot n, offset 0)
+__host__ __device__ __forceinline__ unsigned nl_sentinel(int n) { return nl_entry(n, 0, 0, 0); }
 
 // index i of an array of n elements (debug builds: tested, 0 when outside)
 __device__ __forceinline__ int chk_index(const SpecDev &S, int i, int n) {
@@ -214,8 +223,11 @@ __device__ __forceinline__ int chk_index(const SpecDev &S, int i, int n) {
     return i;
 }
 
-// the atom a list entry names
-__device__ __forceinline__ int nl_atom(const SpecDev &S, unsigned e) { return chk_index(S, nl_j(e), S.n); }
+// the record a list entry names (mixed precision: an atom or the sentinel
+// slot n)
+__device__ __forceinline__ int nl_atom(const SpecDev &S, unsigned e) {
+    return chk_index(S, nl_j(e), S.prec == PTA_PREC_FP64 ? S.n : S.n + 1);
+}
 
 // a count of list entries read by one lane (debug builds: at most `limit`)
 __device__ __forceinline__ int chk_count(const SpecDev &S, int c, int limit) {
