@@ -320,9 +320,29 @@ def batched_leg(P, steps: int = 1, warmup: int = 1):
     b.close()
     for c in ctxs:
         c.close()
+    # the same replica on the plain single-specimen path (alone on the GPU,
+    # its automatic layout): what the replicas would get run one at a time
+    r = reqs[0]
+    solo = P.Ctx(r.n_cells, T0=r.T0, seed=r.seed, precision=1, burst_steps=r.burst_steps,
+                 strain_rate=r.strain_rate)
+    for _ in range(warmup):
+        solo.coarse_step()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        solo.coarse_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_solo = e0.elapsed_time(e1)
+    solo_value = solo.n * 3 * 2000 * steps / (ms_solo / 1e3)
+    solo_lanes = solo.layout()["lanes"]
+    solo.close()
     return {"workload": "batched_64x_n20", "value": value, "unit": "atom-steps/s",
             "atoms": natoms, "specimens": len(ctxs), "coarse_steps": steps, "warmup": warmup,
             "ms_per_coarse_step": ms / steps,
+            "solo_replica": {"value": solo_value, "atoms": solo.n, "lanes": solo_lanes,
+                             "ms_per_coarse_step": ms_solo / steps},
+            "gain_over_solo_replicas": value / solo_value,
             "description": WORKLOADS["batched"]["desc"]}
 
 
