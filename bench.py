@@ -610,8 +610,10 @@ def run_pta(args, wl):
     flops_force = pairs * FLOP_FORCE_PAIR + natoms * (FLOP_ATOM - 5)
     flops_dens = pairs * FLOP_DENSITY_PAIR + natoms * 5
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    # the peak: the larger measured FP32 FMA rate (scalar or packed)
-    peak_tflops = max(peaks["fp32"], peaks["fp32x2"])
+    # the peak of the arithmetic the pair passes run in: the larger measured
+    # FP32 FMA rate (scalar or packed), or the FP64 FMA rate for FP64 specimens
+    mixed = wl["precision"] == 1
+    peak_tflops = max(peaks["fp32"], peaks["fp32x2"]) if mixed else peaks["fp64"]
     ach_force = flops_force / (force_ms / 1e3) / 1e12
     ach_dens = flops_dens / (dens_ms / 1e3) / 1e12
     dominant = ("force", ach_force, force_ms) if force_ms >= dens_ms else ("density", ach_dens,
@@ -702,9 +704,10 @@ def run_pta(args, wl):
                          "traffic": captured_traffic("k_%s_f32" % dominant[0], wl["name"])
                          if wl["precision"] == 1 else None,
                          "peak_source": "measured: FMA-chain probe (pta_measure_fma_rate) "
-                                        "on this GPU, %d SMs, median SM clock %s MHz; the "
-                                        "larger of scalar and packed FP32" % (
-                                            n_sm, peak_clocks["sm_mhz"]),
+                                        "on this GPU, %d SMs, median SM clock %s MHz; %s" % (
+                                            n_sm, peak_clocks["sm_mhz"],
+                                            "the larger of scalar and packed FP32" if mixed
+                                            else "FP64"),
                          "peaks_measured_tflops": peaks,
                          "launch_ms": dominant[2],
                          "kernels_ms_per_iteration": {"rebuild": kt.rebuild_ms / iters,

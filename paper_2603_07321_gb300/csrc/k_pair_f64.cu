@@ -2,6 +2,12 @@
 // (density, then forces with the fused velocity-Verlet epilogue), with every
 // quantity in double.  They serve the plain FP64 form of the method and the
 // parity checks against the FP64 oracle.
+//
+// The pair terms are arranged around y = 1/r from one reciprocal square root
+// (CUDA's rsqrt on double), so that no pair needs a division or a square
+// root: r = r2 y, s = a y, phi_k'(r) / r = (-k s^k y + B_k) y.  FP64 runs at
+// a small fraction of the FP32 rate on this GPU, and a double division or
+// square root costs several fused multiply-adds each.
 #include "k_pair_common.cuh"
 
 namespace pta {
@@ -12,7 +18,20 @@ __device__ __forceinline__ double ipow(double s, int k) {
     return p;
 }
 
-template <int L>
+// s^m and s^n (Sutton-Chen exponents; SC76: n = 7, m = 6)
+template <bool SC76>
+__device__ __forceinline__ void pow_nm(double s, int n, int m, double &sn, double &sm) {
+    if (SC76) {
+        const double s3 = (s * s) * s;
+        sm = s3 * s3;
+        sn = sm * s;
+    } else {
+        sn = ipow(s, n);
+        sm = ipow(s, m);
+    }
+}
+
+template <int L, bool SC76>
 __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__ specs,
                                                      const int *__restrict__ b2s, int force) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -35,8 +54,16 @@ __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__
             const int j = nl_atom(S, (unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pos[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
-            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
-            if (r < P.rc) rho += ipow(P.a / r, P.m) - P.Am + P.Bm * (r - P.rc);
+            const double r2 = (dx * dx + dy * dy) + dz * dz;
+            const double y = rsqrt(r2);
+            const double r = r2 * y;
+            // tested on r2, so that coincident atoms (r2 = 0) still give a
+            // non-finite force rather than no pair
+            if (r2 < P.rc * P.rc) {
+                double sn, sm;
+                pow_nm<SC76>(P.a * y, P.n, P.m, sn, sm);
+                rho += sm - P.Am + P.Bm * (r - P.rc);
+            }
         }
     }
     rho = lane_sum<L>(rho);
@@ -46,7 +73,7 @@ __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__
     }
 }
 
-template <int L>
+template <int L, bool SC76>
 __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ specs,
                                                    const int *__restrict__ b2s, int mode) {
     const SpecDev &S = specs[b2s[blockIdx.x]];
@@ -72,13 +99,17 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
             const int j = nl_atom(S, (unsigned)lst[(k / L) * 32 + (k % L)]);
             const double4_32a pj = pf[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
-            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
-            if (r < P.rc) {
-                const double s = P.a / r;
-                const double sn = ipow(s, P.n), sm = ipow(s, P.m);
-                const double dphn = -(double)P.n / r * sn + P.Bn;
-                const double dphm = -(double)P.m / r * sm + P.Bm;
-                const double g = (P.eps * dphn + (pa.w + pj.w) * dphm) / r;
+            const double r2 = (dx * dx + dy * dy) + dz * dz;
+            const double y = rsqrt(r2);
+            const double r = r2 * y;
+            // tested on r2, so that coincident atoms (r2 = 0) still give a
+            // non-finite force rather than no pair
+            if (r2 < P.rc * P.rc) {
+                double sn, sm;
+                pow_nm<SC76>(P.a * y, P.n, P.m, sn, sm);
+                const double dphn = -(double)P.n * y * sn + P.Bn;
+                const double dphm = -(double)P.m * y * sm + P.Bm;
+                const double g = (P.eps * dphn + (pa.w + pj.w) * dphm) * y;
                 fx += g * dx;
                 fy += g * dy;
                 fz += g * dz;
@@ -163,24 +194,27 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
     step_tail<TPB>(S, lb, S.nblk_pair, ke, pe, rr, d2, 0.0, mode, phase, done, nsteps);
 }
 
-void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st) {
-    switch (g.L) {
-        case 1: k_density_f64<1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 2: k_density_f64<2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 4: k_density_f64<4><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        case 8: k_density_f64<8><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
-        default: k_density_f64<16><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, force); break;
+#define PTA_F64_SWITCH(KER, SC, ARG)                                                   \
+    switch (g.L) {                                                                     \
+        case 1: KER<1, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break;        \
+        case 2: KER<2, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break;        \
+        case 4: KER<4, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break;        \
+        case 8: KER<8, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break;        \
+        default: KER<16, SC><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, ARG); break;      \
     }
+
+void launch_density_f64(const Tab &t, const Group &g, int force, cudaStream_t st) {
+    if (g.sc76)
+        PTA_F64_SWITCH(k_density_f64, true, force)
+    else
+        PTA_F64_SWITCH(k_density_f64, false, force)
 }
 
 void launch_force_f64(const Tab &t, const Group &g, int mode, cudaStream_t st) {
-    switch (g.L) {
-        case 1: k_force_f64<1><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 2: k_force_f64<2><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 4: k_force_f64<4><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        case 8: k_force_f64<8><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-        default: k_force_f64<16><<<g.nblk, TPB, 0, st>>>(t.specs, g.b2s, mode); break;
-    }
+    if (g.sc76)
+        PTA_F64_SWITCH(k_force_f64, true, mode)
+    else
+        PTA_F64_SWITCH(k_force_f64, false, mode)
 }
 
 }  // namespace pta
