@@ -95,6 +95,14 @@ def test_footprint(P):
     assert P.pta_footprint_bytes(bad, p64) == 0
 
 
+def test_atom_count_limit_leaves_room_for_the_sentinel_slot(P):
+    # list entries hold a 23-bit slot index and slot n names the sentinel
+    # record that pads the lists, so a specimen holds fewer than 2^23 atoms
+    p64 = P.default_params()
+    assert P.pta_footprint_bytes(P.make_specimen((128, 128, 128)), p64) == 0   # 2^23 atoms
+    assert P.pta_footprint_bytes(P.make_specimen((49, 127, 337)), p64) > 0     # 2^23 - 4
+
+
 def test_create_rejects_bad_arguments_before_touching_the_gpu(P):
     lib = P.load()
     spec = P.make_specimen((4, 4, 2))  # < 3 cells along the load axis
