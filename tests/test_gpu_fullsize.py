@@ -24,6 +24,10 @@ def test_forces_of_every_atom_of_the_470596_atom_cube(oracle):
     # every atom's force to 1e-5 of itself (floored at the rms force), the
     # rms error to 3e-6; atoms pushed into close pairs carry forces of ~5x
     # the rms, and their absolute errors reach ~1.5e-5 of the rms force
+    e_pe = np.max(np.abs(pe - pe_ref) / np.abs(pe_ref))
+    print("\n470,596-atom cube vs oracle: per-atom force error %.2e, rms %.2e, max/rms %.2e, "
+          "per-atom energy %.2e" % (force_error_atom(f, f_ref), force_error_rms(f, f_ref),
+                                    force_error(f, f_ref), e_pe))
     assert force_error_atom(f, f_ref) < 1e-5
     assert force_error_rms(f, f_ref) < 3e-6
     assert force_error(f, f_ref) < 3e-5
