@@ -337,7 +337,10 @@ void pta_batch_destroy(pta_batch *batch);
 /* d_eps[count]: per-member grip increments (strain units). */
 int pta_batch_apply_strain(pta_batch *batch, const double *d_eps);
 /* nsteps[count]: per-member burst lengths (0 leaves a member idle);
- * out[count] receives the averages. */
+ * out[count] receives the averages.  A failure of single members
+ * (PTA_ENEIGH_OVERFLOW, PTA_ENAN, PTA_ERANGE, PTA_ECHECK in out[i].status)
+ * is returned as the first such status after every out[i] is filled; the
+ * other members' results are valid and the batch stays usable. */
 int pta_batch_fine_burst(pta_batch *batch, const int64_t *nsteps, pta_averages *out);
 /* One coarse step of every member (each with its own strain rate and
  * burst length), out[count]; members that have not yet run their initial
@@ -347,7 +350,8 @@ int pta_batch_coarse_step(pta_batch *batch, pta_coarse_result *out);
  * initial bursts have not run runs them (its result has t = 0, v = v(0),
  * source[] = -1); every other member runs one coarse step.  This is the
  * unit of continuous batching: members at different stages share the same
- * launches. */
+ * launches.  Member failures are reported as for pta_batch_fine_burst:
+ * out[i].status per member, the first one returned, the others valid. */
 int pta_batch_tick(pta_batch *batch, pta_coarse_result *out);
 int pta_batch_set_timing(pta_batch *batch, int enable);
 int pta_batch_get_timing(pta_batch *batch, pta_kernel_times *out);

@@ -431,11 +431,17 @@ def pta_batch_apply_strain(b, d_eps):
     _check(load().pta_batch_apply_strain(b, _dptr(arr)), "pta_batch_apply_strain")
 
 
+# statuses that concern single members of a batch call: the call has filled
+# every member's result (its own status in it), the others' are valid
+MEMBER_STATUSES = frozenset((-4, -5, -7, -10))
+
+
 def pta_batch_fine_burst(b, nsteps):
     ns = np.ascontiguousarray(nsteps, dtype=np.int64)
     out = (Averages * len(ns))()
-    _check(load().pta_batch_fine_burst(b, ns.ctypes.data_as(_P(ctypes.c_int64)), out),
-           "pta_batch_fine_burst")
+    rc = load().pta_batch_fine_burst(b, ns.ctypes.data_as(_P(ctypes.c_int64)), out)
+    if rc not in MEMBER_STATUSES:
+        _check(rc, "pta_batch_fine_burst")
     return list(out)
 
 
@@ -447,7 +453,9 @@ def pta_batch_coarse_step(b, count):
 
 def pta_batch_tick(b, count):
     out = (CoarseResult * count)()
-    _check(load().pta_batch_tick(b, out), "pta_batch_tick")
+    rc = load().pta_batch_tick(b, out)
+    if rc not in MEMBER_STATUSES:
+        _check(rc, "pta_batch_tick")
     return list(out)
 
 

@@ -34,6 +34,7 @@ class Request:
     burst_steps: int = 2000
     precision: int = 1
     lanes: int = 0        # threads per atom (0: the library's per-specimen choice)
+    neigh_cap: int = 0    # Verlet-list capacity per atom (0: the library's default)
 
 
 @dataclass
@@ -156,6 +157,17 @@ class Scheduler:
             if out.get("error"):
                 self._retire(rid, "failed", now, out["error"])
                 continue
+            if out.get("recovered"):
+                # the engine replaced the specimen (restored from its state
+                # before this tick, with more list capacity): it repeats
+                # the tick next time; its memory grew
+                slot["handle"] = out["handle"]
+                grow = int(out.get("bytes", slot["bytes"])) - slot["bytes"]
+                slot["bytes"] += grow
+                self.used += grow
+                self._event("request_recovered", tag=rid, reason=out.get("reason", ""),
+                            neigh_cap=out.get("neigh_cap"), bytes=slot["bytes"])
+                continue
             res.tick_latency_s.append(dt)
             res.atom_steps += out["atom_steps"]
             if not out.get("initial"):
@@ -208,11 +220,25 @@ class Scheduler:
                 "failed": sum(1 for r in self.results.values() if r.status == "failed")}
 
 
+PTA_ENEIGH_OVERFLOW = -4
+
+
 class GPUEngine:
     """The device side: one pta_ctx per specimen, one pta_batch over the live
-    set, rebuilt when the set changes."""
+    set, rebuilt when the set changes.
 
-    def __init__(self, stream=None, replicas_hint: int = 16):
+    With `recover`, every live specimen's state is checkpointed (to host
+    memory) before each tick; a specimen whose tick reports a neighbour-list
+    overflow (an atom gathered more neighbours than its list holds, e.g.
+    under strong compression) is recreated with twice the list capacity,
+    restored from that checkpoint and handed back to the scheduler, which
+    runs its tick again with the next one.  List capacity changes only where
+    entries are stored, not their order, so the recovered specimen continues
+    exactly as one created with the larger capacity would have.  At most
+    `max_regrow` recoveries per specimen; after that the failure stands."""
+
+    def __init__(self, stream=None, replicas_hint: int = 16, recover: bool = True,
+                 max_regrow: int = 4):
         from . import (PTAError, Batch, Ctx, default_params, make_specimen,
                        pta_footprint_bytes)
         self._PTAError, self._Batch, self._Ctx = PTAError, Batch, Ctx
@@ -221,6 +247,9 @@ class GPUEngine:
         self.batch_members: list = []
         self.stream = stream
         self.replicas_hint = replicas_hint
+        self.recover = recover
+        self.max_regrow = max_regrow
+        self._info: dict = {}       # id(ctx) -> {"req", "neigh_cap", "regrow"}
 
     def validate(self, req: Request) -> str:
         if req.n_cells < 3 or req.n_cells > 126:
@@ -231,9 +260,10 @@ class GPUEngine:
             return "target strain must be positive"
         return ""
 
-    def _p(self, req):
+    def _p(self, req, neigh_cap: int = 0):
         kw = dict(precision=req.precision, burst_steps=req.burst_steps,
-                  strain_rate=req.strain_rate, lanes=req.lanes)
+                  strain_rate=req.strain_rate, lanes=req.lanes,
+                  neigh_cap=neigh_cap or req.neigh_cap)
         if not req.lanes:
             # the autotuner's layout for this size among ~replicas_hint live specimens
             from .tune import lookup
@@ -242,17 +272,18 @@ class GPUEngine:
                 kw.update(hit)
         return self._params(**kw)
 
-    def footprint(self, req: Request) -> int:
-        return int(self._fp(self._spec(req.n_cells), self._p(req)))
+    def footprint(self, req: Request, neigh_cap: int = 0) -> int:
+        return int(self._fp(self._spec(req.n_cells), self._p(req, neigh_cap)))
 
-    def create(self, req: Request):
+    def create(self, req: Request, neigh_cap: int = 0):
         try:
-            ctx = self._Ctx(req.n_cells, T0=req.T0, seed=req.seed, params=self._p(req),
-                            stream=self.stream)
+            ctx = self._Ctx(req.n_cells, T0=req.T0, seed=req.seed,
+                            params=self._p(req, neigh_cap), stream=self.stream)
         except self._PTAError as e:
             if e.status == -2:
                 raise MemoryError(str(e))
             raise
+        self._info[id(ctx)] = {"req": req, "regrow": 0}
         return ctx
 
     def destroy(self, ctx):
@@ -260,7 +291,30 @@ class GPUEngine:
             self.batch.close()
             self.batch = None
             self.batch_members = []
+        self._info.pop(id(ctx), None)
         ctx.close()
+
+    def _regrow(self, ctx, blob):
+        """A replacement for ctx with twice its list capacity, in the state
+        `blob` (taken before the failed tick), or None."""
+        info = self._info.get(id(ctx))
+        if info is None or info["regrow"] >= self.max_regrow:
+            return None
+        req = info["req"]
+        cap = 2 * int(ctx.layout()["neigh_cap"])
+        try:
+            new = self.create(req, neigh_cap=cap)
+        except (MemoryError, self._PTAError):
+            return None
+        try:
+            new.restore(blob)
+        except self._PTAError:
+            self.destroy(new)
+            return None
+        self._info[id(new)]["regrow"] = info["regrow"] + 1
+        self.destroy(ctx)
+        return {"recovered": True, "handle": new, "neigh_cap": cap, "atom_steps": 0,
+                "bytes": self.footprint(req, cap), "reason": "neighbour-list overflow"}
 
     def tick(self, ctxs):
         if self.batch is None or self.batch_members != list(ctxs):
@@ -268,12 +322,18 @@ class GPUEngine:
                 self.batch.close()
             self.batch = self._Batch(ctxs)
             self.batch_members = list(ctxs)
+        blobs = [c.save() for c in ctxs] if self.recover else None
         try:
             res = self.batch.tick()
         except self._PTAError as e:
             return [{"error": str(e)} for _ in ctxs]
         out = []
-        for c, r in zip(ctxs, res):
+        for i, (c, r) in enumerate(zip(ctxs, res)):
+            if r.status == PTA_ENEIGH_OVERFLOW and self.recover:
+                rec = self._regrow(c, blobs[i])
+                if rec is not None:
+                    out.append(rec)
+                    continue
             if r.status != 0:
                 out.append({"error": "status %d" % r.status})
                 continue

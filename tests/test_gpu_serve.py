@@ -64,3 +64,37 @@ def test_batch_of_uneven_served_sizes_stays_finite():
     b.close()
     for c in ctxs:
         c.close()
+
+
+def test_neighbour_overflow_is_recovered_with_more_list_capacity():
+    # request 1 asks for a list capacity (64 entries per atom) far below the
+    # ~200 neighbours within the list radius: its first tick overflows; the
+    # engine restores it from its state before that tick with twice the
+    # capacity, until it fits.  Capacity changes where entries are stored,
+    # not their order, so its curve is bit-identical to the same request at
+    # the default capacity; request 0 in the same batch is undisturbed.
+    def mk(rid, cap):
+        r = _req(rid, 6, 1e-2, 0.025)
+        r.seed = 70
+        r.neigh_cap = cap
+        return r
+    _, ref = _serve([mk(0, 0)], slots=1)
+    s, res = _serve([mk(0, 0), mk(1, 64)], slots=2)
+    assert res[0].status == "done" and res[1].status == "done"
+    for rid in (0, 1):
+        assert len(res[rid].curve) == len(ref[0].curve) > 0
+        for (s1, v1, src1), (s2, v2, src2) in zip(res[rid].curve, ref[0].curve):
+            assert s1 == s2 and v1 == v2 and src1 == src2
+    assert s.used == 0
+
+
+def test_neighbour_overflow_without_recovery_fails_only_that_specimen():
+    gpu_package()
+    eng = GPUEngine(recover=False)
+    s = Scheduler(eng, mem_budget_bytes=8 << 30, max_slots=2)
+    ok, bad = _req(0, 6, 1e-2, 0.025), _req(1, 6, 1e-2, 0.025)
+    bad.neigh_cap = 64
+    res = s.run([ok, bad], realtime=False)
+    eng.close()
+    assert res[1].status == "failed" and "-4" in res[1].error
+    assert res[0].status == "done" and len(res[0].curve) > 0

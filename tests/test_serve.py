@@ -3,6 +3,7 @@
 Faults are injected on the host: invalid requests, an allocation that fails
 at admission, and a specimen whose tick reports an error."""
 import itertools
+import json
 
 import pytest
 
@@ -13,10 +14,11 @@ class FakeEngine:
     """Advances each specimen's strain by rate * h per tick (the first tick
     of a specimen is its initial one); footprint = 1000 bytes per cell^3."""
 
-    def __init__(self, fail_create=(), fail_tick=(), oom_once=()):
+    def __init__(self, fail_create=(), fail_tick=(), oom_once=(), overflow_once=()):
         self.fail_create = set(fail_create)
         self.fail_tick = set(fail_tick)
         self.oom_once = set(oom_once)
+        self.overflow_once = set(overflow_once)
         self.state = {}
         self.created = []
         self.destroyed = []
@@ -49,6 +51,19 @@ class FakeEngine:
             s = self.state[h]
             if h in self.fail_tick and s["ticks"] >= 1:
                 out.append({"error": "simulated burst failure"})
+                continue
+            if h in self.overflow_once and s["ticks"] >= 1:
+                # the real engine restores the specimen from its state before
+                # this tick into a new one with more list memory: same state,
+                # new handle, the tick not counted
+                self.overflow_once.discard(h)
+                new = ("regrown", h)
+                self.state[new] = dict(s)
+                self.state.pop(h)
+                self.destroyed.append(h)
+                out.append({"recovered": True, "handle": new, "atom_steps": 0,
+                            "bytes": 2 * self.footprint(s["req"]), "neigh_cap": 64,
+                            "reason": "neighbour-list overflow"})
                 continue
             s["ticks"] += 1
             r = s["req"]
@@ -134,6 +149,25 @@ def test_failing_member_does_not_disturb_the_others():
     assert 1 in eng.destroyed
     assert s.results[0].status == "done"
     assert s.results[0].curve == alone.results[0].curve
+
+
+def test_recovered_member_repeats_its_tick_under_a_new_handle(tmp_path):
+    from paper_2603_07321_gb300.metrics import JsonlLog
+    alone = Scheduler(FakeEngine(), mem_budget_bytes=10 ** 9, clock=_clock())
+    alone.run([req(1, target=0.05)], realtime=False)
+    eng = FakeEngine(overflow_once={1})
+    log = JsonlLog(str(tmp_path / "m.jsonl"))
+    s = Scheduler(eng, mem_budget_bytes=10 ** 9, clock=_clock(), log=log)
+    s.run([req(0, target=0.05), req(1, target=0.05)], realtime=False)
+    log.close()
+    # the recovered specimen finishes with the same curve as alone, one tick later
+    assert s.results[1].status == "done" and s.results[0].status == "done"
+    assert s.results[1].curve == alone.results[1].curve
+    assert ("regrown", 1) in eng.destroyed and 1 in eng.destroyed
+    assert s.used == 0 and not s.live
+    recs = [json.loads(line) for line in open(tmp_path / "m.jsonl")]
+    ev = [r for r in recs if r.get("kind") == "request_recovered"]
+    assert len(ev) == 1 and ev[0]["tag"] == 1 and ev[0]["bytes"] == 2 * 1000 * 10 ** 3
 
 
 def test_latency_statistics():
