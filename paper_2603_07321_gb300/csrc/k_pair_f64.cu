@@ -55,11 +55,12 @@ __global__ void __launch_bounds__(TPB) k_density_f64(const SpecDev *__restrict__
             const double4_32a pj = pos[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r2 = (dx * dx + dy * dy) + dz * dz;
-            const double y = rsqrt(r2);
-            const double r = r2 * y;
-            // tested on r2, so that coincident atoms (r2 = 0) still give a
-            // non-finite force rather than no pair
+            // tested on r2 (the reciprocal square root only for pairs within
+            // rc), so that coincident atoms (r2 = 0) still give a non-finite
+            // result rather than no pair
             if (r2 < P.rc * P.rc) {
+                const double y = rsqrt(r2);
+                const double r = r2 * y;
                 double sn, sm;
                 pow_nm<SC76>(P.a * y, P.n, P.m, sn, sm);
                 rho += sm - P.Am + P.Bm * (r - P.rc);
@@ -100,11 +101,10 @@ __global__ void __launch_bounds__(TPB) k_force_f64(const SpecDev *__restrict__ s
             const double4_32a pj = pf[j];
             const double dx = pj.x - pa.x, dy = pj.y - pa.y, dz = pj.z - pa.z;
             const double r2 = (dx * dx + dy * dy) + dz * dz;
-            const double y = rsqrt(r2);
-            const double r = r2 * y;
-            // tested on r2, so that coincident atoms (r2 = 0) still give a
-            // non-finite force rather than no pair
+            // tested on r2, as in the density pass
             if (r2 < P.rc * P.rc) {
+                const double y = rsqrt(r2);
+                const double r = r2 * y;
                 double sn, sm;
                 pow_nm<SC76>(P.a * y, P.n, P.m, sn, sm);
                 const double dphn = -(double)P.n * y * sn + P.Bn;
