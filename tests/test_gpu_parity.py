@@ -63,10 +63,14 @@ def ctx_pot(oracle, ctx):
     return oracle.Potential(eps=p.eps, c=p.c, a=p.a, rc=p.rc, n=p.n, m=p.m)
 
 
+@pytest.mark.parametrize("margin", [0.0, -1.0])       # inner list (default margin) / none
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
-def test_forces_mixed(P, oracle, lanes):
+def test_forces_mixed(P, oracle, lanes, margin):
+    # every lane's list (inner or Verlet) ends with sentinel entries up to a
+    # multiple of four, whatever the lanes per atom
     shape = (6, 5, 7)
-    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes)
+    ctx = P.Ctx(shape, precision=P.PREC_MIXED, lanes=lanes, prune_margin=margin)
+    assert ctx.layout()["pruned_list"] == (margin == 0.0)
     pos = on_grid(PI.gaussian_jitter_fcc(shape, 0.1, seed=10 + lanes))
     ctx.set_state(pos, np.zeros_like(pos))
     f, pe, _ = ctx.forces()
