@@ -359,3 +359,43 @@ def test_atom_beyond_the_cell_grid_is_reported(P, oracle):
             ctx.fine_burst(5)
         assert e.value.status == -7
         ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(1, 1, 3), (1, 2, 5), (2, 1, 9), (8, 8, 4)])
+def test_thinnest_specimens_match_the_oracle(P, oracle, prec, shape):
+    # the smallest specimens the boundary accepts (one or two cells across,
+    # three or more along the load axis, a plate): fewer atoms than a warp or
+    # a block, cell grids of one or two cells, lists shorter than the loops'
+    # four-entry groups; in the 1 x 1 x 3 cube every atom is a grip atom, so
+    # no velocity is drawn and nothing moves
+    ctx = P.Ctx(shape, T0=0.0, seed=1, precision=prec)
+    pos = on_grid(PI.jittered_fcc(shape, 0.2, seed=sum(shape)))
+    ctx.set_state(pos, np.zeros_like(pos))
+    c_gpu, l_gpu = ctx.neighbours(cap=512)
+    rl = ctx.potential.rc + ctx.params.skin
+    c_ref, l_ref = oracle.pairs(pos, rl, cap=512, method="brute")
+    assert np.array_equal(c_gpu, c_ref)
+    assert sorted_rows(c_gpu, l_gpu) == sorted_rows(c_ref, l_ref)
+    f, pe, _ = ctx.forces()
+    f_ref, pe_ref, _ = oracle.eam(pos, ctx_pot(oracle, ctx))
+    assert force_error(f, f_ref) < (1e-10 if prec == 0 else 1e-5)
+    assert np.max(np.abs(pe - pe_ref) / np.abs(pe_ref)) < (1e-11 if prec == 0 else 1e-5)
+    ctx.close()
+    # 100 steps at 300 K after a tension step, against the oracle's burst
+    ctx, spec = _pair(P, oracle, shape, prec, seed=5)
+    ctx.apply_strain(2e-3)
+    spec.apply_strain(2e-3)
+    a = ctx.fine_burst(100)
+    s_gpu = ctx.series()
+    s_ref = spec.burst(100)
+    p_gpu, _ = ctx.get_state()
+    assert a.status == 0 and a.nsteps == 100
+    if prec == 0:
+        assert np.max(np.abs(p_gpu - spec.pos)) < 1e-8
+        assert np.allclose(s_gpu, s_ref, rtol=1e-9, atol=1e-9)
+    else:
+        assert np.max(np.abs(p_gpu - spec.pos)) < 1e-4 * 4.05 * max(shape)
+        assert np.all(np.abs(s_gpu[:, :2] - s_ref[:, :2]) <= 1e-5 * np.abs(s_ref[:, :2]) + 1e-9)
+        assert np.max(np.abs(s_gpu[:, 2] - s_ref[:, 2])) < 1e-3
+    ctx.close()
