@@ -377,7 +377,10 @@ static size_t footprint(const Sizes &z, int prec) {
         add(16 * n);                 // pref
     }
     add(4 * n);                      // nn
-    add(64 * (size_t)std::max(z.nblk_pair, z.nblk_atom));  // part
+    {
+        const size_t nb = (size_t)std::max(z.nblk_pair, z.nblk_atom);
+        add(64 * (nb + 2 * (nb / 32 + 1)));  // part: block and group partials, group counters
+    }
     add(24 * (size_t)z.series_cap);  // series
     add(32 * n);                     // eval_out
     if (z.mean_pos) add(32 * n);     // rsum
@@ -1043,7 +1046,12 @@ static int ctx_alloc_all(pta_ctx *c, const Sizes &z) {
         AL(pref, 16 * n, float4 *);
     }
     AL(nn, 4 * n, int *);
-    AL(part, 64 * (size_t)std::max(z.nblk_pair, z.nblk_atom), double *);
+    {
+        // block partials (8 doubles per block), then per group of 32 blocks
+        // its partial (8 doubles) and its counter
+        const size_t nb = (size_t)std::max(z.nblk_pair, z.nblk_atom);
+        AL(part, 64 * (nb + 2 * (nb / 32 + 1)), double *);
+    }
     AL(series, 24 * (size_t)z.series_cap, double *);
     AL(eval_out, 32 * n, double *);
     if (z.mean_pos) {
